@@ -1,0 +1,193 @@
+"""FP64 CPU oracle of the GP-WENO finite-difference scheme.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import, call, link or
+run anything in this package.  The product path (the CUDA library and its
+Python binding) never touches it, and the two share no code: the oracle has
+its own arbitrary-precision table precompute (``gp_tables.py``, Python
+``decimal``) and its own per-face scheme (``euler_oracle.c``, plain FP64 C).
+
+Parity status per function (pins are in ``tests/test_oracle_*.py``):
+  gp_tables.tables          pinned (flat-limit Lagrange weights, direct-solve vs
+                            eigen form, moment defects, linear-weight consistency)
+  euler_oracle gp_weno      pinned (equal beta => omega = gamma, step data,
+                            scaling, mirror symmetry)
+  euler_oracle roe/flux     pinned (L R = I, R diag(lambda) L = Jacobian,
+                            Roe property)
+  corrected_flux            pinned (exact for degree-5 flux primitives)
+  oracle_rhs / rk3          pinned (free-stream preservation, conservation,
+                            mirror and rotation symmetry, smooth-vortex order)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from . import gp_tables
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "euler_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libeuler_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with the host gcc (plain -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("R", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
+                ("wl", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("wr", ctypes.c_void_p),
+                ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(_Cfg)
+            dp = ctypes.c_void_p
+            lib.oracle_rhs.argtypes = [P, dp, dp]
+            lib.oracle_rhs.restype = ctypes.c_int
+            lib.oracle_rk3_step.argtypes = [P, dp, ctypes.c_double]
+            lib.oracle_rk3_step.restype = ctypes.c_int
+            lib.oracle_max_rate.argtypes = [P, dp]
+            lib.oracle_max_rate.restype = ctypes.c_double
+            lib.oracle_face.argtypes = [P, ctypes.c_int, dp, dp, dp, dp]
+            lib.oracle_face.restype = ctypes.c_int
+            lib.oracle_roe.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
+            lib.oracle_roe.restype = ctypes.c_int
+            lib.oracle_gp_weno.argtypes = [P, dp, ctypes.c_int]
+            lib.oracle_gp_weno.restype = ctypes.c_double
+            lib.oracle_corrected_flux.argtypes = [dp]
+            lib.oracle_corrected_flux.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Oracle:
+    """One configured problem: grid, boundary conditions, R, l/Delta, sigma/Delta, gas gamma.
+
+    ``shape`` is the interior grid (nx,), (ny, nx) or (nz, ny, nx) in array
+    order; ``dx`` is the spacing per axis in (x, y, z) order; ``bc`` is a
+    sequence of (lo, hi) pairs in (x, y, z) order with 'periodic' or 'outflow'.
+    """
+
+    def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
+                 gamma=1.4, eps=1e-36, p=2):
+        self.lib = _load()
+        shape = tuple(int(s) for s in shape)
+        self.ndim = len(shape)
+        self.shape = shape
+        self.nc = self.ndim + 2
+        t = gp_tables.scheme_tables(R, ell_over_dx, sigma_over_dx)
+        self.tables = t
+        self._keep = [np.ascontiguousarray(t[k], dtype=np.float64) for k in ("wl", "gl", "wr", "gr", "Kinv")]
+        c = _Cfg()
+        c.ndim = self.ndim
+        n_xyz = list(reversed(shape)) + [1] * (3 - self.ndim)
+        for a in range(3):
+            c.n[a] = n_xyz[a]
+            c.dx[a] = float(dx[a]) if a < self.ndim else 1.0
+            lo, hi = bc[a] if a < self.ndim else ("outflow", "outflow")
+            c.bc_lo[a] = 0 if lo == "periodic" else 1
+            c.bc_hi[a] = 0 if hi == "periodic" else 1
+        c.R = int(R)
+        c.gamma = float(gamma)
+        c.eps = float(eps)
+        c.p = int(p)
+        c.wl, c.gl, c.wr, c.gr, c.Kinv = [a.ctypes.data for a in self._keep]
+        self.cfg = c
+        self.R = int(R)
+        self.gamma = float(gamma)
+
+    def _state(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        assert U.shape == (self.nc,) + self.shape, (U.shape, self.shape)
+        return U
+
+    def rhs(self, U):
+        """L(U) of Eq. disc_fd; raises if a non-physical state was met."""
+        U = self._state(U)
+        out = np.empty_like(U)
+        if self.lib.oracle_rhs(ctypes.byref(self.cfg), _ptr(U), _ptr(out)):
+            raise FloatingPointError("non-physical state in oracle rhs")
+        return out
+
+    def rk3_step(self, U, dt):
+        U = self._state(U).copy()
+        if self.lib.oracle_rk3_step(ctypes.byref(self.cfg), _ptr(U), float(dt)):
+            raise FloatingPointError("non-physical state in oracle rk3 step")
+        return U
+
+    def max_rate(self, U):
+        U = self._state(U)
+        return float(self.lib.oracle_max_rate(ctypes.byref(self.cfg), _ptr(U)))
+
+    def cfl_dt(self, U, cfl):
+        return cfl / self.max_rate(U)
+
+    def run(self, U, dt, nsteps):
+        U = self._state(U).copy()
+        for _ in range(int(nsteps)):
+            if self.lib.oracle_rk3_step(ctypes.byref(self.cfg), _ptr(U), float(dt)):
+                raise FloatingPointError("non-physical state in oracle run")
+        return U
+
+    def face(self, stencil, d=0):
+        """Riemann states and flux at the middle face of a (2R+2, nc) stencil along axis d (x=0)."""
+        st = np.ascontiguousarray(stencil, dtype=np.float64)
+        assert st.shape == (2 * self.R + 2, self.nc)
+        uL = np.zeros(self.nc)
+        uR = np.zeros(self.nc)
+        F = np.zeros(self.nc)
+        ok = self.lib.oracle_face(ctypes.byref(self.cfg), int(d), _ptr(st), _ptr(uL), _ptr(uR), _ptr(F))
+        if not ok:
+            raise FloatingPointError("non-physical face state")
+        return uL, uR, F
+
+    def gp_weno(self, f, right=False):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (2 * self.R + 1,)
+        return float(self.lib.oracle_gp_weno(ctypes.byref(self.cfg), _ptr(f), int(bool(right))))
+
+
+def roe_eigensystem(uL, uR, gamma=1.4):
+    """(Rm, Lm) at the Roe average of two conserved states given normal-first."""
+    lib = _load()
+    uL = np.ascontiguousarray(uL, dtype=np.float64)
+    uR = np.ascontiguousarray(uR, dtype=np.float64)
+    nc = uL.shape[0]
+    Rm = np.zeros((nc, nc))
+    Lm = np.zeros((nc, nc))
+    if not lib.oracle_roe(nc, float(gamma), _ptr(uL), _ptr(uR), _ptr(Rm), _ptr(Lm)):
+        raise FloatingPointError("non-physical Roe state")
+    return Rm, Lm
+
+
+def corrected_flux(F5):
+    lib = _load()
+    F5 = np.ascontiguousarray(F5, dtype=np.float64)
+    assert F5.shape == (5,)
+    return float(lib.oracle_corrected_flux(_ptr(F5)))

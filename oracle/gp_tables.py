@@ -1,0 +1,214 @@
+"""GP-WENO weight tables in arbitrary precision -- part of the test oracle.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports this module;
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may use it.  It shares no code with the CUDA library (which has
+its own double-double precompute in C++).
+
+Everything here follows the pre-simulation step of the paper's stepwise
+algorithm (Section 4, step 1(a)-(d)), written as the plain definitions, with
+Python's ``decimal`` module at 100 significant digits so that even the
+ill-conditioned covariance systems at large l/Delta (cond K ~ 1e25 at R=3,
+l/Delta=96) are solved to far below FP64 rounding.
+
+Units: every length is in units of the grid spacing Delta, so the big stencil
+S_R has points x_j = j, j = -R..R, centred on cell i (Eq. 2R1-stencil), and the
+face-centre prediction point is x* = +1/2 (face i+1/2) or x* = -1/2 (face
+i-1/2).
+
+Tables returned (all numpy float64 after rounding the decimal results):
+  w_big[j]      GP weights on S_R, w = K^{-1} k*            (Eqs. kmat, kstar, q-intrp)
+  w_sub[m][j]   GP weights on sub-stencil S_{m+1}            (Eqs. sub-stencil, candidate_interp)
+  gamma[m]      least-squares linear weights of M gamma = w  (Eqs. gamm-system, M-mat)
+  Kinv_sigma    inverse of the sub-stencil covariance K_m built with sigma
+                instead of l (Section 3.4); beta_m = f^T Kinv f (Eq. gp-smooth)
+  eig_sigma     (lambda, V) of that covariance, for the eigen form of beta
+                (Eq. beta-eigen), used only to pin the definition form.
+Sub-stencil m (0-based) holds the points -R+m .. m (Eq. sub-stencil with
+m_paper = m+1).
+"""
+from __future__ import annotations
+
+import decimal
+from decimal import Decimal
+from functools import lru_cache
+
+import numpy as np
+
+PREC = 100
+
+
+def _ctx():
+    return decimal.Context(prec=PREC)
+
+
+def _D(x) -> Decimal:
+    if isinstance(x, Decimal):
+        return x
+    if isinstance(x, float):
+        # exact binary value of the double, no rounding
+        return Decimal(x)
+    return Decimal(x)
+
+
+def se_kernel(a: Decimal, b: Decimal, ell: Decimal) -> Decimal:
+    """Squared-exponential kernel with Sigma = 1 (Eq. se; Sigma cancels, Section 3.1)."""
+    with decimal.localcontext(_ctx()):
+        d = a - b
+        return (-(d * d) / (2 * ell * ell)).exp()
+
+
+def solve(A, b):
+    """Gaussian elimination with partial pivoting on decimal matrices (plain textbook algorithm)."""
+    n = len(A)
+    with decimal.localcontext(_ctx()):
+        M = [list(map(_D, row)) + [_D(b[i])] for i, row in enumerate(A)]
+        for c in range(n):
+            p = max(range(c, n), key=lambda r: abs(M[r][c]))
+            if M[p][c] == 0:
+                raise ZeroDivisionError("singular matrix")
+            M[c], M[p] = M[p], M[c]
+            for r in range(c + 1, n):
+                f = M[r][c] / M[c][c]
+                if f != 0:
+                    for k in range(c, n + 1):
+                        M[r][k] -= f * M[c][k]
+        x = [Decimal(0)] * n
+        for r in range(n - 1, -1, -1):
+            s = M[r][n]
+            for k in range(r + 1, n):
+                s -= M[r][k] * x[k]
+            x[r] = s / M[r][r]
+        return x
+
+
+def inverse(A):
+    n = len(A)
+    cols = [solve(A, [Decimal(1) if i == j else Decimal(0) for i in range(n)]) for j in range(n)]
+    return [[cols[j][i] for j in range(n)] for i in range(n)]
+
+
+def least_squares(M, rhs):
+    """argmin ||M g - rhs||_2 through the normal equations (M^T M) g = M^T rhs.
+
+    At 100 digits the squared condition number of the (2R+1)x(R+1) matrix M
+    (whose columns are weight vectors) costs nothing measurable."""
+    rows, cols = len(M), len(M[0])
+    with decimal.localcontext(_ctx()):
+        MtM = [[sum((M[r][a] * M[r][b] for r in range(rows)), Decimal(0)) for b in range(cols)]
+               for a in range(cols)]
+        Mtr = [sum((M[r][a] * rhs[r] for r in range(rows)), Decimal(0)) for a in range(cols)]
+    return solve(MtM, Mtr)
+
+
+def jacobi_eigen(A, sweeps=100):
+    """Cyclic Jacobi eigen-decomposition of a symmetric decimal matrix.
+
+    Returns (lam, V) with A V[:,h] = lam[h] V[:,h], eigenvalues ascending.
+    Textbook rotation formulas (Golub & Van Loan, Alg. 8.4.2)."""
+    n = len(A)
+    with decimal.localcontext(_ctx()):
+        a = [[_D(x) for x in row] for row in A]
+        v = [[Decimal(1) if i == j else Decimal(0) for j in range(n)] for i in range(n)]
+        tiny = Decimal(10) ** (-(PREC - 10))
+        for _ in range(sweeps):
+            off = sum(a[i][j] * a[i][j] for i in range(n) for j in range(n) if i != j)
+            if off.sqrt() < tiny:
+                break
+            for p in range(n - 1):
+                for q in range(p + 1, n):
+                    if a[p][q] == 0:
+                        continue
+                    theta = (a[q][q] - a[p][p]) / (2 * a[p][q])
+                    sign = 1 if theta >= 0 else -1
+                    t = sign / (abs(theta) + (theta * theta + 1).sqrt())
+                    c = 1 / (t * t + 1).sqrt()
+                    s = t * c
+                    for k in range(n):
+                        akp, akq = a[k][p], a[k][q]
+                        a[k][p] = c * akp - s * akq
+                        a[k][q] = s * akp + c * akq
+                    for k in range(n):
+                        apk, aqk = a[p][k], a[q][k]
+                        a[p][k] = c * apk - s * aqk
+                        a[q][k] = s * apk + c * aqk
+                    for k in range(n):
+                        vkp, vkq = v[k][p], v[k][q]
+                        v[k][p] = c * vkp - s * vkq
+                        v[k][q] = s * vkp + c * vkq
+        lam = [a[i][i] for i in range(n)]
+        order = sorted(range(n), key=lambda i: lam[i])
+        return [lam[i] for i in order], [[v[k][i] for i in order] for k in range(n)]
+
+
+def covariance(points, ell):
+    """[K]_jk = K(x_j, x_k) (Eq. kmat)."""
+    return [[se_kernel(a, b, ell) for b in points] for a in points]
+
+
+def kstar(points, xs, ell):
+    """[k*]_k = K(x*, x_k) (Eq. kstar)."""
+    return [se_kernel(xs, b, ell) for b in points]
+
+
+def gp_weights(points, xs, ell):
+    """w = K^{-1} k*, so that the GP posterior mean at x* is w^T f (Eqs. zero-mean, q-intrp)."""
+    return solve(covariance(points, ell), kstar(points, xs, ell))
+
+
+def m_matrix(w_sub, R):
+    """The (2R+1)x(R+1) matrix of Eq. M-mat: column n carries w_n in rows n..n+R."""
+    M = [[Decimal(0)] * (R + 1) for _ in range(2 * R + 1)]
+    for n in range(R + 1):
+        for j in range(R + 1):
+            M[n + j][n] = w_sub[n][j]
+    return M
+
+
+@lru_cache(maxsize=None)
+def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str):
+    ell, sigma, xs = Decimal(ell_s), Decimal(sigma_s), Decimal(xs_s)
+    big = [Decimal(j) for j in range(-R, R + 1)]
+    w_big = gp_weights(big, xs, ell)
+    w_sub = []
+    for m in range(R + 1):
+        pts = [Decimal(j) for j in range(-R + m, m + 1)]
+        w_sub.append(gp_weights(pts, xs, ell))
+    M = m_matrix(w_sub, R)
+    gam = least_squares(M, w_big)
+    # smoothness-indicator covariance: any sub-stencil (they are all identical, Eq. beta-eigen text)
+    pts0 = [Decimal(j) for j in range(R + 1)]
+    Ks = covariance(pts0, sigma)
+    Kinv = inverse(Ks)
+    lam, V = jacobi_eigen(Ks)
+    return dict(w_big=w_big, w_sub=w_sub, gamma=gam, M=M, K_sigma=Ks, Kinv_sigma=Kinv,
+                lam_sigma=lam, V_sigma=V, K_ell=covariance(big, ell))
+
+
+def tables_decimal(R: int, ell_over_dx, sigma_over_dx, xstar):
+    """Decimal tables (see module docstring) for one prediction point x* in units of Delta."""
+    return _tables_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)))
+
+
+def _f64(x):
+    if isinstance(x, list):
+        return np.array([_f64(v) for v in x], dtype=np.float64)
+    return float(x)
+
+
+def tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5) -> dict:
+    """The same tables rounded to float64 numpy arrays."""
+    t = tables_decimal(R, ell_over_dx, sigma_over_dx, xstar)
+    out = {k: _f64(v) for k, v in t.items()}
+    out["R"] = int(R)
+    return out
+
+
+def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0) -> dict:
+    """Everything the per-face oracle needs: left-state tables (x* = +1/2 from
+    the stencil of cell i), right-state tables (x* = -1/2 from the stencil of
+    cell i+1, computed directly, not by reversal) and K_m(sigma)^{-1}."""
+    tl = tables(R, ell_over_dx, sigma_over_dx, 0.5)
+    tr = tables(R, ell_over_dx, sigma_over_dx, -0.5)
+    return dict(R=int(R), wl=tl["w_sub"], gl=tl["gamma"], wr=tr["w_sub"], gr=tr["gamma"],
+                Kinv=tl["Kinv_sigma"], w_big_l=tl["w_big"], w_big_r=tr["w_big"])
