@@ -1,0 +1,166 @@
+/*
+ * gpweno.h -- C ABI of the GB300 (sm_103a) GP-WENO finite-difference library
+ * for the compressible Euler equations.
+ *
+ * The library evaluates, per face and per Runge-Kutta stage, the conservative
+ * flux divergence of the GP-WENO FD-Prim scheme of Reyes, Lee, Graziani and
+ * Tzeferacos (arXiv:1808.04960) and fuses it with the SSP-RK3 stage update:
+ *
+ *   - Riemann states at every face by GP-WENO interpolation of characteristic
+ *     variables (Sections 3.2-3.3; the stepwise algorithm of Section 4, step 2),
+ *     with the Roe-averaged eigenvectors of the two cells sharing the face;
+ *   - local Lax-Friedrichs face flux on those states (Eq. riemann_prob);
+ *   - the high-order correction with alpha = -1/24, beta = 3/640
+ *     (Eqs. numFlux_cor, FD-ders);
+ *   - the flux difference (Eq. disc_fd) and the SSP-RK3 stage combination
+ *     (Section 2, step 5; Shu-Osher form).
+ *
+ * Conventions for every entry point:
+ *   - No exception or C++ type crosses this boundary; every function returns
+ *     a gpweno_status.  gpweno_last_error() gives a thread-local message for
+ *     the last non-OK status raised on the calling thread.
+ *   - State arrays are caller-owned DEVICE buffers in structure-of-arrays
+ *     layout [nc][nz][ny][nx] (x fastest), interior cells only (no ghost
+ *     cells: boundary conditions are applied when tiles are loaded),
+ *     nc = ndim + 2 components (rho, rho*u_1, ..., rho*u_ndim, E), element
+ *     type float (GPWENO_F32) or double (GPWENO_F64) as chosen at plan
+ *     creation.  Buffers must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Launches are asynchronous; errors of earlier launches surface at the
+ *     next call or at gpweno_flags().  Step functions allocate nothing and do
+ *     not synchronise.
+ *   - A plan owns its weight tables and a small device workspace (flags,
+ *     wavespeed maxima); it is not thread-safe to use one plan from two
+ *     streams at once.
+ */
+#ifndef GPWENO_H
+#define GPWENO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPWENO_OK = 0,
+    GPWENO_ERR_ARG = 1,          /* invalid argument (message says which) */
+    GPWENO_ERR_PRECOMPUTE = 2,   /* GP tables ill-conditioned even in double-double */
+    GPWENO_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    GPWENO_ERR_NONPHYSICAL = 4,  /* rho <= 0, p <= 0 or NaN met by a kernel */
+    GPWENO_ERR_TIMEOUT = 5       /* reserved: bounded device wait gave up */
+} gpweno_status;
+
+typedef enum { GPWENO_F32 = 0, GPWENO_F64 = 1 } gpweno_dtype;
+typedef enum { GPWENO_BC_PERIODIC = 0, GPWENO_BC_OUTFLOW = 1 } gpweno_bc;
+
+typedef struct gpweno_plan_s *gpweno_plan;   /* opaque, owned by the library */
+
+/* Grid description.  ndim in {1,2,3}; n[d] cells and spacing dx[d] for
+ * d < ndim (x, y, z order); bc_lo/bc_hi per dimension.  Periodic must be set
+ * on both sides of a dimension or on neither. */
+typedef struct {
+    int ndim;
+    int n[3];
+    double dx[3];
+    int bc_lo[3];
+    int bc_hi[3];
+} gpweno_dims;
+
+/* Options (NULL = defaults).
+ *   sigma_over_dx  length hyperparameter of the smoothness-indicator kernel
+ *                  (Section 3.4; default 3.0).  Must be > 1.
+ *   eps, p         WENO-JS constants of Eq. weights (default 1e-36 and 2; p in {1,2}).
+ *   dtype          GPWENO_F32 (bulk arithmetic in FP32, tables rounded from
+ *                  double-double) or GPWENO_F64.
+ *   cfl            if > 0, gpweno_rk3_step with a dt_dev pointer also writes
+ *                  the next step's dt = cfl / sum_d max(|u_d|+c)/dx_d of the
+ *                  new state into *dt_dev (fused into the last stage).
+ *   flux_form      0 = FD-Prim with local Lax-Friedrichs face flux (only value). */
+typedef struct {
+    double sigma_over_dx;
+    double eps;
+    int p;
+    int dtype;
+    double cfl;
+    int flux_form;
+} gpweno_opts;
+
+void gpweno_default_opts(gpweno_opts *opts);
+
+/* Build a plan: GP radius R in {1,2,3} (stencil 2R+1 points, R+1 sub-stencils
+ * of R+1 points, Eq. sub-stencil), length hyperparameter l/dx (Eqs. se, kmat,
+ * kstar; must satisfy l/dx >= 1), grid `dims`, ratio of specific heats
+ * `gamma_gas` (> 1).  The GP weights w_m (Eq. candidate_interp), linear
+ * weights gamma_m (Eq. gamm-system, least squares), and the smoothness
+ * factors P_h = v_h / sqrt(lambda_h) of K_m(sigma) (Eq. beta-eigen) are
+ * computed in double-double arithmetic on the host (Section 4, step 1),
+ * rounded to the plan's dtype and kept with the plan.  Allocates a few
+ * hundred bytes of device memory on the current device; the plan must be
+ * used on that device.  Returns GPWENO_ERR_PRECOMPUTE if the covariance
+ * system is too ill-conditioned for double-double. */
+gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, const gpweno_dims *dims,
+                                 double gamma_gas, const gpweno_opts *opts);
+gpweno_status gpweno_plan_destroy(gpweno_plan plan);
+
+/* Copy the plan's tables (double precision, before rounding to the plan's
+ * dtype) to host arrays; any pointer may be NULL.  All refer to the
+ * prediction point x* = x_i + dx/2 (left state of face i+1/2):
+ *   w_m   (R+1)*(R+1): w_m[m*(R+1)+j] = weight of point j of sub-stencil m
+ *         (sub-stencil m covers cells i-R+m .. i+m), Eq. candidate_interp;
+ *   gam   R+1 linear weights (Eqs. gamm-system, M-mat);
+ *   P     (R+1)*(R+1): P[h*(R+1)+j] = v_h[j] / sqrt(lambda_h), eigenpairs of
+ *         K_m(sigma) ascending (Eq. beta-eigen);
+ *   w_big 2R+1 GP weights on the full stencil (Eq. q-intrp). */
+gpweno_status gpweno_plan_tables(gpweno_plan plan, double *w_m, double *gam, double *P, double *w_big);
+
+/* Host-only: the double-double GP tables of gpweno_plan_create without a
+ * plan or a device (for checking the precompute on machines without a GPU).
+ * Left-state tables as in gpweno_plan_tables; w_m_r, gam_r are the tables
+ * of the right state of face i+1/2 (x* = x_{i+1} - dx/2, stencil of cell
+ * i+1).  Any output pointer may be NULL.  Returns GPWENO_ERR_ARG or
+ * GPWENO_ERR_PRECOMPUTE as gpweno_plan_create would. */
+gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_m, double *gam, double *P,
+                               double *w_big, double *w_m_r, double *gam_r);
+
+/* dUdt = L(U): the right-hand side of Eq. disc_fd with the corrected fluxes
+ * of Eq. numFlux_cor.  U, dUdt: device state arrays (see conventions);
+ * they must not overlap. */
+gpweno_status gpweno_rhs(gpweno_plan plan, const void *U, void *dUdt, void *stream);
+
+/* One SSP-RK3 step in place on U (three fused stage launches):
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U <- 1/3 U + 2/3 (U2 + dt L(U2)).
+ * scratch: caller-owned device buffer of 2 state sizes (U1, U2).
+ * dt_dev: NULL to use `dt`; otherwise a device double holding dt, read by
+ * the kernels (graph-capturable), and, when the plan's cfl > 0, overwritten
+ * after the step with the CFL time step of the new state. */
+gpweno_status gpweno_rk3_step(gpweno_plan plan, void *U, void *scratch, double dt, void *dt_dev, void *stream);
+
+/* *dt_dev (device double) = cfl / sum_d max over cells of (|u_d| + c)/dx_d. */
+gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *dt_dev, void *stream);
+
+/* Read and clear the plan's sticky non-physical flag (synchronises the
+ * device).  *nonphysical = 1 if any kernel since the last read met rho <= 0,
+ * p <= 0 or a NaN; returns GPWENO_ERR_CUDA if an earlier launch failed. */
+gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
+
+/* Batched 2D stepping: one persistent launch per RK stage serves n
+ * independent 2D plans of possibly different grid size, R, l/dx and sigma
+ * (all plans must share dtype and gamma).  The batch keeps references to the
+ * plans' tables, which must outlive it.  tune_cache: path of a JSON file of
+ * tuned schedule parameters, or NULL for the built-in cost model. */
+gpweno_status gpweno_plan_batch(gpweno_plan *out_batch, const gpweno_plan *plans, int n, const char *tune_cache);
+
+/* One SSP-RK3 step of every instance of a batch plan: U[k], scratch[k]
+ * (2 state sizes) are device buffers of instance k; dt_dev: device array of
+ * n doubles (instance time steps).  Three launches in total. */
+gpweno_status gpweno_batch_rk3_step(gpweno_plan batch, void *const *U, void *const *scratch, const void *dt_dev,
+                                    void *stream);
+
+/* Number of kernel launches the last step function issued (for launch accounting). */
+int gpweno_last_launch_count(void);
+
+const char *gpweno_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPWENO_H */

@@ -1,0 +1,156 @@
+// Host-side launch of the stage kernels for one arithmetic type: table
+// conversion, schedule (strip width, segment height, grid), kernel selection.
+#pragma once
+#include <algorithm>
+
+#include "plan.h"
+#include "stage.cuh"
+
+namespace gpweno {
+
+constexpr int kNT2D = 256;
+constexpr int kNT1D = 128;
+
+template <typename T, int R>
+FaceTables<T, R> make_tables(const gpweno_plan_s *p)
+{
+    FaceTables<T, R> t;
+    const int S = R + 1;
+    for (int m = 0; m < S; ++m)
+        for (int j = 0; j < S; ++j) {
+            t.wl[m][j] = (T)p->tab.wl[m * S + j];
+            t.wr[m][j] = (T)p->tab.wr[m * S + j];
+            t.P[m][j] = (T)p->tab.P[m * S + j];
+        }
+    for (int m = 0; m < S; ++m) {
+        t.gl[m] = (T)p->tab.gl[m];
+        t.gr[m] = (T)p->tab.gr[m];
+    }
+    t.eps = (T)p->opts.eps;
+    t.gamma = (T)p->gamma;
+    t.p = p->opts.p;
+    return t;
+}
+
+// Choose the strip width and the number of row segments of the 2D kernel:
+// strips as wide as the block allows, then the segment count that minimises
+// (waves of CTAs) x (rows per segment + 5 warm-up y-face rows).
+inline Schedule schedule2d(int nx, int ny, int nt, int slots)
+{
+    Schedule s;
+    const int wmax = nt - 5;
+    s.nstrips = (nx + wmax - 1) / wmax;
+    s.W = (nx + s.nstrips - 1) / s.nstrips;
+    double best = 1e300;
+    int best_seg = 1;
+    const int segmax = std::max(1, std::min(ny, 8 * slots));
+    for (int nseg = 1; nseg <= segmax; ++nseg) {
+        const int H = (ny + nseg - 1) / nseg;
+        const int items = s.nstrips * nseg;
+        const int waves = (items + slots - 1) / slots;
+        const double cost = (double)waves * (H + 5.5);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_seg = nseg;
+        }
+    }
+    s.nseg = best_seg;
+    s.H = (ny + best_seg - 1) / best_seg;
+    s.nseg = (ny + s.H - 1) / s.H;
+    s.grid = std::min(s.nstrips * s.nseg, slots);
+    return s;
+}
+
+template <typename T>
+StageArgs<T> base_args(const gpweno_plan_s *p)
+{
+    StageArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = p->dims.n[d];
+        a.per[d] = p->dims.bc_lo[d] == GPWENO_BC_PERIODIC ? 1 : 0;
+        a.idx[d] = (T)(1.0 / p->dims.dx[d]);
+    }
+    a.flags = reinterpret_cast<int *>(p->ws + 3);
+    return a;
+}
+
+template <typename T, int R>
+gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t st)
+{
+    StageArgs<T> a = a0;
+    const FaceTables<T, R> tb = make_tables<T, R>(p);
+    if (p->dims.ndim == 2) {
+        constexpr int NT = kNT2D;
+        const size_t smem = stage2d_smem_bytes<T, R, NT>();
+        auto kern = stage2d_kernel<T, R, NT>;
+        static int occ = 0;   // per instantiation: resident CTAs per SM
+        if (!occ) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "stage2d smem attribute");
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+            if (e != cudaSuccess || occ < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                                                              "stage2d occupancy");
+        }
+        Schedule s = schedule2d(a.n[0], a.n[1], NT, occ * p->num_sms);
+        a.W = s.W;
+        a.nstrips = s.nstrips;
+        a.H = s.H;
+        a.nseg = s.nseg;
+        p->sched = s;
+        kern<<<s.grid, NT, smem, st>>>(a, tb);
+    } else {
+        constexpr int NT = kNT1D;
+        const size_t smem = stage1d_smem_bytes<T, R, NT>();
+        auto kern = stage1d_kernel<T, R, NT>;
+        a.nstrips = (a.n[0] + (NT - 5) - 1) / (NT - 5);
+        a.W = (a.n[0] + a.nstrips - 1) / a.nstrips;
+        a.H = 1;
+        a.nseg = 1;
+        kern<<<a.nstrips, NT, smem, st>>>(a, tb);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    count_launch(1);
+    return GPWENO_OK;
+}
+
+template <typename T>
+gpweno_status launch_stage_T(gpweno_plan p, const void *U, const void *U0, void *out, double a0, double b, int mode,
+                             double dt, const double *dt_dev, bool want_rate, cudaStream_t st)
+{
+    StageArgs<T> a = base_args<T>(p);
+    a.U = static_cast<const T *>(U);
+    a.U0 = static_cast<const T *>(U0);
+    a.out = static_cast<T *>(out);
+    a.a0 = (T)a0;
+    a.b = (T)b;
+    a.mode = mode;
+    a.dt = dt;
+    a.dt_dev = dt_dev;
+    a.rate = want_rate ? p->ws : nullptr;
+    switch (p->R) {
+    case 1: return launch_stage_R<T, 1>(p, a, st);
+    case 2: return launch_stage_R<T, 2>(p, a, st);
+    case 3: return launch_stage_R<T, 3>(p, a, st);
+    default: set_error("R=%d not compiled", p->R); return GPWENO_ERR_ARG;
+    }
+}
+
+template <typename T>
+gpweno_status launch_max_rate_T(gpweno_plan p, const void *U, cudaStream_t st)
+{
+    StageArgs<T> a = base_args<T>(p);
+    a.rate = p->ws;
+    const int blocks = (int)std::min<long>((p->ncell + 255) / 256, 4L * p->num_sms);
+    if (p->dims.ndim == 2)
+        max_rate_kernel<T, 4><<<blocks, 256, 0, st>>>(static_cast<const T *>(U), p->ncell, a, (T)p->gamma);
+    else
+        max_rate_kernel<T, 3><<<blocks, 256, 0, st>>>(static_cast<const T *>(U), p->ncell, a, (T)p->gamma);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "max-rate kernel launch");
+    count_launch(1);
+    return GPWENO_OK;
+}
+
+}  // namespace gpweno

@@ -1,0 +1,32 @@
+// Host-side GP weight precompute in double-double arithmetic (Section 4, step 1).
+#pragma once
+#include <cstddef>
+
+namespace gpweno {
+
+constexpr int kMaxR = 3;
+constexpr int kMaxS = kMaxR + 1;           // points per sub-stencil
+constexpr int kMaxBig = 2 * kMaxR + 1;     // points of the full stencil
+
+struct GpTables {
+    int R;
+    // left state of face i+1/2 (x* = +1/2 from the stencil of cell i)
+    double wl[kMaxS * kMaxS];   // [m][j]
+    double gl[kMaxS];
+    double wbig_l[kMaxBig];
+    // right state of face i+1/2 (x* = -1/2 from the stencil of cell i+1)
+    double wr[kMaxS * kMaxS];
+    double gr[kMaxS];
+    double wbig_r[kMaxBig];
+    // smoothness factors P[h][j] = v_h[j] / sqrt(lambda_h) of K_m(sigma), lambda ascending
+    double P[kMaxS * kMaxS];
+    double lambda[kMaxS];
+    double ls_residual;          // ||M gamma - w||_2 of the left-state system
+    double cond_estimate;        // rough condition estimate of K(l)
+};
+
+// Returns 0 on success; otherwise writes a message to err and returns
+// 1 (bad argument) or 2 (ill-conditioned beyond double-double).
+int gp_precompute(int R, double ell_over_dx, double sigma_over_dx, GpTables *out, char *err, std::size_t errlen);
+
+}  // namespace gpweno

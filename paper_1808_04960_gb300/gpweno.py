@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/gpweno.h (ctypes; argument marshalling only).
+
+Every step of the numerical path runs in the CUDA library ``libgpweno.so``;
+this module only checks tensor shapes/dtypes/devices, passes raw pointers and
+the current CUDA stream, and turns status codes into exceptions.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the
+library is missing, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpweno.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gpweno.h")
+
+OK, ERR_ARG, ERR_PRECOMPUTE, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT = range(6)
+F32, F64 = 0, 1
+PERIODIC, OUTFLOW = 0, 1
+
+
+class GpwenoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gpweno status {status}: {msg}")
+        self.status = status
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("sigma_over_dx", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("cfl", ctypes.c_double), ("flux_form", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libgpweno.so (built by ``paper_1808_04960_gb300.build``).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} not found: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        dp = ctypes.POINTER(ctypes.c_double)
+        sigs = {
+            "gpweno_default_opts": (None, [ctypes.POINTER(Opts)]),
+            "gpweno_plan_create": (i, [ctypes.POINTER(vp), i, d, ctypes.POINTER(Dims), d, ctypes.POINTER(Opts)]),
+            "gpweno_plan_destroy": (i, [vp]),
+            "gpweno_plan_tables": (i, [vp, dp, dp, dp, dp]),
+            "gpweno_gp_tables": (i, [i, d, d, dp, dp, dp, dp, dp, dp]),
+            "gpweno_rhs": (i, [vp, vp, vp, vp]),
+            "gpweno_rk3_step": (i, [vp, vp, vp, d, vp, vp]),
+            "gpweno_cfl_dt": (i, [vp, vp, d, vp, vp]),
+            "gpweno_flags": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
+            "gpweno_plan_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, ctypes.c_char_p]),
+            "gpweno_batch_rk3_step": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]),
+            "gpweno_last_launch_count": (i, []),
+            "gpweno_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/gpweno.h."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpweno_[a-z0-9_]+)\s*\(", src)))
+
+
+def _check(status, what=""):
+    if status != OK:
+        msg = load().gpweno_last_error().decode(errors="replace")
+        raise GpwenoError(status, f"{what}: {msg}" if what else msg)
+
+
+def last_launch_count() -> int:
+    return int(load().gpweno_last_launch_count())
+
+
+def _dbl(n):
+    return (ctypes.c_double * n)()
+
+
+def gp_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0) -> dict:
+    """The library's double-double tables, computed on the host (no device needed)."""
+    import numpy as np
+    S = R + 1
+    wm, g, P, wb, wmr, gr = _dbl(S * S), _dbl(S), _dbl(S * S), _dbl(2 * R + 1), _dbl(S * S), _dbl(S)
+    _check(load().gpweno_gp_tables(int(R), float(ell_over_dx), float(sigma_over_dx), wm, g, P, wb, wmr, gr),
+           "gpweno_gp_tables")
+    a = lambda x, shape: np.array(list(x), dtype=np.float64).reshape(shape)
+    return dict(w_sub=a(wm, (S, S)), gamma=a(g, (S,)), P=a(P, (S, S)), w_big=a(wb, (2 * R + 1,)),
+                w_sub_r=a(wmr, (S, S)), gamma_r=a(gr, (S,)))
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _bc_code(b):
+    if isinstance(b, int):
+        return b
+    return {"periodic": PERIODIC, "outflow": OUTFLOW}[b]
+
+
+class Plan:
+    """A GP-WENO plan for one grid (see gpweno_plan_create).
+
+    shape: interior grid in array order ((nx,), (ny, nx)); dx: spacing in
+    (x, y) order; bc: (lo, hi) pairs in (x, y) order, 'periodic' or 'outflow'.
+    """
+
+    def __init__(self, R, ell_over_dx, shape, dx, bc, gamma=1.4, sigma_over_dx=3.0, eps=1e-36, p=2,
+                 dtype="f32", cfl=0.0):
+        import torch
+        self.lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        self.ndim = len(self.shape)
+        self.nc = self.ndim + 2
+        self.R = int(R)
+        self.dtype = {"f32": torch.float32, "f64": torch.float64}[dtype]
+        self.cfl = float(cfl)
+        dims = Dims()
+        dims.ndim = self.ndim
+        n_xyz = list(reversed(self.shape))
+        for a in range(3):
+            dims.n[a] = n_xyz[a] if a < self.ndim else 1
+            dims.dx[a] = float(dx[a]) if a < self.ndim else 1.0
+            lo, hi = bc[a] if a < self.ndim else ("outflow", "outflow")
+            dims.bc_lo[a] = _bc_code(lo)
+            dims.bc_hi[a] = _bc_code(hi)
+        opts = Opts()
+        self.lib.gpweno_default_opts(ctypes.byref(opts))
+        opts.sigma_over_dx = float(sigma_over_dx)
+        opts.eps = float(eps)
+        opts.p = int(p)
+        opts.dtype = F32 if dtype == "f32" else F64
+        opts.cfl = float(cfl)
+        h = ctypes.c_void_p()
+        _check(self.lib.gpweno_plan_create(ctypes.byref(h), self.R, float(ell_over_dx), ctypes.byref(dims),
+                                           float(gamma), ctypes.byref(opts)), "gpweno_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.gpweno_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_state(self, U, name="U"):
+        import torch
+        if not isinstance(U, torch.Tensor) or not U.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if U.dtype != self.dtype or tuple(U.shape) != (self.nc,) + self.shape or not U.is_contiguous():
+            raise ValueError(f"{name} must be contiguous {self.dtype} of shape {(self.nc,) + self.shape}, "
+                             f"got {U.dtype} {tuple(U.shape)}")
+
+    def empty_state(self, n=1):
+        import torch
+        return torch.empty((n, self.nc) + self.shape, dtype=self.dtype, device="cuda")
+
+    def tables(self) -> dict:
+        import numpy as np
+        S = self.R + 1
+        wm, g, P, wb = _dbl(S * S), _dbl(S), _dbl(S * S), _dbl(2 * self.R + 1)
+        _check(self.lib.gpweno_plan_tables(self.handle, wm, g, P, wb), "gpweno_plan_tables")
+        a = lambda x, shape: np.array(list(x), dtype=np.float64).reshape(shape)
+        return dict(w_sub=a(wm, (S, S)), gamma=a(g, (S,)), P=a(P, (S, S)), w_big=a(wb, (2 * self.R + 1,)))
+
+    def rhs(self, U, out=None, stream=None):
+        """out = L(U) (Eq. disc_fd)."""
+        import torch
+        self._check_state(U)
+        if out is None:
+            out = torch.empty_like(U)
+        self._check_state(out, "out")
+        _check(self.lib.gpweno_rhs(self.handle, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream)), "gpweno_rhs")
+        return out
+
+    def rk3_step(self, U, scratch, dt=0.0, dt_dev=None, stream=None):
+        """One SSP-RK3 step in place on U.  scratch: tensor of shape (2, nc, ...) of the plan's dtype.
+        dt_dev: optional CUDA float64 scalar tensor holding dt (updated with the CFL dt if cfl > 0)."""
+        import torch
+        self._check_state(U)
+        if (scratch.dtype != self.dtype or tuple(scratch.shape) != (2, self.nc) + self.shape
+                or not scratch.is_contiguous() or not scratch.is_cuda):
+            raise ValueError("scratch must be a contiguous CUDA tensor of shape (2, nc, ...) and the plan's dtype")
+        dptr = None
+        if dt_dev is not None:
+            if dt_dev.dtype != torch.float64 or not dt_dev.is_cuda or dt_dev.numel() != 1:
+                raise ValueError("dt_dev must be a CUDA float64 tensor with one element")
+            dptr = ctypes.c_void_p(dt_dev.data_ptr())
+        _check(self.lib.gpweno_rk3_step(self.handle, ctypes.c_void_p(U.data_ptr()),
+                                        ctypes.c_void_p(scratch.data_ptr()), float(dt), dptr,
+                                        _stream_handle(stream)), "gpweno_rk3_step")
+        return U
+
+    def cfl_dt(self, U, cfl, dt_dev, stream=None):
+        import torch
+        self._check_state(U)
+        if dt_dev.dtype != torch.float64 or not dt_dev.is_cuda or dt_dev.numel() != 1:
+            raise ValueError("dt_dev must be a CUDA float64 tensor with one element")
+        _check(self.lib.gpweno_cfl_dt(self.handle, ctypes.c_void_p(U.data_ptr()), float(cfl),
+                                      ctypes.c_void_p(dt_dev.data_ptr()), _stream_handle(stream)), "gpweno_cfl_dt")
+        return dt_dev
+
+    def flags(self) -> int:
+        v = ctypes.c_int(0)
+        _check(self.lib.gpweno_flags(self.handle, ctypes.byref(v)), "gpweno_flags")
+        return int(v.value)
+
+
+class BatchPlan:
+    """Batched 2D stepping over several plans (gpweno_plan_batch)."""
+
+    def __init__(self, plans, tune_cache=None):
+        self.lib = load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self.lib.gpweno_plan_batch(ctypes.byref(h), arr, len(self.plans),
+                                          tune_cache.encode() if tune_cache else None), "gpweno_plan_batch")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.gpweno_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rk3_step(self, Us, scratches, dt_dev, stream=None):
+        import torch
+        n = len(self.plans)
+        if len(Us) != n or len(scratches) != n:
+            raise ValueError("one state and one scratch tensor per instance")
+        for p, U, s in zip(self.plans, Us, scratches):
+            p._check_state(U)
+            if tuple(s.shape) != (2, p.nc) + p.shape or s.dtype != p.dtype or not s.is_contiguous():
+                raise ValueError("bad scratch tensor")
+        if dt_dev.dtype != torch.float64 or dt_dev.numel() != n or not dt_dev.is_cuda:
+            raise ValueError("dt_dev must be a CUDA float64 tensor with one entry per instance")
+        ua = (ctypes.c_void_p * n)(*[u.data_ptr() for u in Us])
+        sa = (ctypes.c_void_p * n)(*[s.data_ptr() for s in scratches])
+        _check(self.lib.gpweno_batch_rk3_step(self.handle, ua, sa, ctypes.c_void_p(dt_dev.data_ptr()),
+                                              _stream_handle(stream)), "gpweno_batch_rk3_step")

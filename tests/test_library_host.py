@@ -1,0 +1,82 @@
+"""Host-side checks of the CUDA library that need no GPU: it builds, loads,
+exports every function include/gpweno.h declares, its double-double GP
+precompute agrees with the oracle's independent 100-digit tables, and its
+argument checks reject bad plans before touching a device."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gp_tables as OT
+from paper_1808_04960_gb300 import build as libbuild
+from paper_1808_04960_gb300 import gpweno
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return gpweno.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = gpweno.header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("R,ell,sigma", [(1, 12.0, 3.0), (2, 12.0, 3.0), (3, 12.0, 3.0), (2, 6.0, 1.5),
+                                         (3, 24.0, 3.0), (1, 24.0, 24.0), (2, 12.0, 12.0), (3, 6.0, 3.0)])
+def test_dd_tables_match_oracle(lib, R, ell, sigma):
+    """Two independent precomputes (double-double Cholesky/Jacobi in C++ and 100-digit
+    decimal Gauss/Jacobi in Python) agree to near FP64 rounding."""
+    t = gpweno.gp_tables(R, ell, sigma)
+    ol = OT.tables(R, ell, sigma, 0.5)
+    orr = OT.tables(R, ell, sigma, -0.5)
+    tol = 1e-13
+    np.testing.assert_allclose(t["w_sub"], ol["w_sub"], rtol=0, atol=tol * np.abs(ol["w_sub"]).max())
+    np.testing.assert_allclose(t["w_big"], ol["w_big"], rtol=0, atol=tol * np.abs(ol["w_big"]).max())
+    np.testing.assert_allclose(t["gamma"], ol["gamma"], rtol=tol, atol=0)
+    np.testing.assert_allclose(t["w_sub_r"], orr["w_sub"], rtol=0, atol=tol * np.abs(orr["w_sub"]).max())
+    np.testing.assert_allclose(t["gamma_r"], orr["gamma"], rtol=tol, atol=0)
+    # P^T P = K_m(sigma)^{-1}, whatever the eigenvector signs
+    PtP = t["P"].T @ t["P"]
+    np.testing.assert_allclose(PtP, ol["Kinv_sigma"], rtol=0, atol=1e-12 * np.abs(ol["Kinv_sigma"]).max())
+    # rows of P are orthogonal directions scaled by 1/sqrt(lambda), ascending lambda
+    lam = 1.0 / np.sum(t["P"] ** 2, axis=1)
+    np.testing.assert_allclose(lam, ol["lam_sigma"], rtol=1e-12)
+
+
+def test_dd_tables_flat_limit(lib):
+    t = gpweno.gp_tables(2, 1000.0, 3.0)
+    np.testing.assert_allclose(t["gamma"], [1 / 16, 10 / 16, 5 / 16], atol=1e-5)
+
+
+@pytest.mark.parametrize("args,status", [((0, 12.0, 3.0), gpweno.ERR_ARG), ((4, 12.0, 3.0), gpweno.ERR_ARG),
+                                         ((2, 0.5, 3.0), gpweno.ERR_ARG), ((2, 12.0, 1.0), gpweno.ERR_ARG),
+                                         ((3, 1000.0, 3.0), gpweno.ERR_PRECOMPUTE)])
+def test_precompute_rejects(lib, args, status):
+    with pytest.raises(gpweno.GpwenoError) as e:
+        gpweno.gp_tables(*args)
+    assert e.value.status == status
+
+
+def test_plan_argument_checks_before_device(lib):
+    """Invalid plans are refused with GPWENO_ERR_ARG before any CUDA call."""
+    bad = [
+        dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "outflow"),) * 2),
+        dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, -0.1), bc=(("periodic", "periodic"),) * 2),
+        dict(R=5, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2),
+        dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2, p=3),
+        dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2, gamma=1.0),
+        dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2,
+             eps=1e-40),
+    ]
+    for kw in bad:
+        with pytest.raises(gpweno.GpwenoError) as e:
+            gpweno.Plan(**kw)
+        assert e.value.status == gpweno.ERR_ARG, kw
+
+
+def test_batch_needs_plans(lib):
+    with pytest.raises(gpweno.GpwenoError):
+        gpweno.BatchPlan([])
