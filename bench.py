@@ -1,0 +1,370 @@
+"""Throughput benchmark of the GP-WENO SSP-RK3 step on GB300.
+
+Workload (default): 2D isentropic vortex, periodic [-5,5]^2, 1024^2 cells,
+GP-R2, l = 12 dx, sigma = 3 dx, gamma = 1.4, fixed dt = 0.4 / max rate of the
+initial state; FP32 is the headline, FP64 is timed beside it.  A step is one
+SSP-RK3 step (three fused stage launches).  Metric: cell-updates/s per RK
+stage = cells x 3 x steps / time.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GP-WENO cell-updates/s per RK stage, FP32 vs FP64, at L1 err vs FP64 oracle"
+UNIT = "cell-updates/s"
+# roofline constants: FP32 FMA lanes x SMs x max SM clock, 2 FLOP per FMA
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def flops_per_cell_stage(R: int, ndim: int = 2) -> float:
+    """Algorithmic FP32 operations per cell and RK stage of the GP-WENO stage (FMA = 2)."""
+    from paper_1808_04960_gb300 import costmodel
+    return costmodel.flops_per_cell_stage(R, ndim)
+
+
+def hbm_bytes_per_cell_stage(esz: int, nc: int = 4) -> float:
+    """Algorithmic HBM bytes per cell and stage, averaged over the three stages:
+    read the stage input once, write the result once, read U^n in stages 2 and 3."""
+    return esz * nc * (2.0 + 2.0 / 3.0)
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_steps(plan, U, scratch, dt, steps, stream, flush, graph=None):
+    """Per-step CUDA-event times (ms) of `steps` RK3 steps; L2 flushed between steps outside the events."""
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if graph is not None:
+            graph.replay()
+        else:
+            plan.rk3_step(U, scratch, dt=dt, stream=stream)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1808_04960_gb300 import build as libbuild
+    from paper_1808_04960_gb300 import gpweno, workloads
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    n, R = args.grid, args.R
+    U0, meta = workloads.isentropic_vortex(n)
+    cells = n * n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
+
+    # fixed dt of the run from the initial state (computed on the device)
+    p64 = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype="f64")
+    U64 = torch.from_numpy(U0).to("cuda", torch.float64)
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p64.cfl_dt(U64, 0.4, dt_dev)
+    dt = float(dt_dev.item())
+
+    results = {}
+    states = {}
+    for dtype in args.dtypes.split(","):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        plan = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
+        U = torch.from_numpy(U0).to("cuda", tdt).contiguous()
+        scratch = torch.empty((2,) + tuple(U.shape), dtype=tdt, device="cuda")
+        steps = args.steps if dtype == "f32" else max(3, min(args.steps, args.fp64_steps))
+        for _ in range(args.warmup):
+            plan.rk3_step(U, scratch, dt=dt, stream=stream)
+        launches = gpweno.last_launch_count()
+        graph = None
+        if args.graph:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                plan.rk3_step(U, scratch, dt=dt)
+            graph.replay()   # one more warm step through the graph
+        torch.cuda.synchronize()
+        barrier(ws)
+        with ClockSampler(local) as clk:
+            t_list = time_steps(plan, U, scratch, dt, steps, stream, flush, graph)
+        barrier(ws)
+        total_ms = max_over_ranks(sum(t_list), ws)
+        results[dtype] = dict(ms_per_step=total_ms / steps, steps=steps, launches_per_step=launches,
+                              value=ws * cells * 3 * steps / (total_ms * 1e-3), clocks=clk.summary(),
+                              kernel_ms=statistics.mean(t_list) / 3.0)
+        states[dtype] = (plan, U, scratch)
+        assert plan.flags() == 0, "non-physical state in benchmark run"
+
+    # accuracy of FP32 against the FP64 path after the same number of steps from the same data
+    acc = None
+    if "f64" in states:
+        n32 = args.warmup + (1 if args.graph else 0) + results["f32"]["steps"]
+        p32, _, s32 = states["f32"]
+        U32 = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+        U64 = torch.from_numpy(U0).to("cuda", torch.float64).contiguous()
+        s64 = states["f64"][2]
+        for _ in range(n32):
+            p32.rk3_step(U32, s32, dt=dt)
+            states["f64"][0].rk3_step(U64, s64, dt=dt)
+        d = (U32.double() - U64).abs()
+        acc = {"steps": n32, "l1_f32_vs_f64_gpu": float(d.mean()), "linf_f32_vs_f64_gpu": float(d.max())}
+
+    # end to end through the public API: pinned host state in, step, state out, every step
+    plan, U, scratch = states["f32"]
+    host = torch.from_numpy(U0.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
+    nb = host.numel() * host.element_size()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        U.copy_(host, non_blocking=True)
+        plan.rk3_step(U, scratch, dt=dt, stream=stream)
+        host_out.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    e2e = {"value": ws * cells * 3 * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
+           "d2h_bytes_per_step": nb, "ms_per_step": e2e_ms / args.steps}
+
+    if rank != 0:
+        return None
+    peaks, peak_kind = read_peaks()
+    r32 = results["f32"]
+    kernel_s = r32["kernel_ms"] * 1e-3
+    flops = flops_per_cell_stage(R) * cells
+    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / kernel_s / 1e12
+    hbm_ach = hbm_bytes_per_cell_stage(4) * cells / kernel_s / 1e9
+    line = {
+        "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"2D isentropic vortex {n}x{n} periodic [-5,5]^2, GP-R{R}, l=12dx, sigma=3dx, "
+                               "SSP-RK3 fixed dt (CFL 0.4)", "grid": [n, n], "R": R, "ell_over_dx": 12.0,
+                   "sigma_over_dx": 3.0, "dt": dt, "cuda_graph": bool(args.graph),
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "fp64": ({"value": results["f64"]["value"], "ms_per_step": results["f64"]["ms_per_step"],
+                  "steps": results["f64"]["steps"], "fp32_over_fp64": r32["value"] / results["f64"]["value"]}
+                 if "f64" in results else None),
+        "accuracy": acc,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": f"stage2d_kernel<float,{R},256>",
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "flops_per_cell_stage": flops_per_cell_stage(R)},
+        "roofline_hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": hbm_ach / peaks.get("hbm_gbs"), "peak_kind": peak_kind,
+                         "bytes_per_cell_stage": hbm_bytes_per_cell_stage(4)},
+        "e2e": e2e,
+        "gpu_launches": r32["launches_per_step"] * args.steps,
+        "clocks": r32["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, dt)
+    return line
+
+
+def cpu_baseline(args, dt_full, gpu_compare=True):
+    """The FP64 oracle, as it stands, on a bounded sample: the vortex at `--cpu-grid`^2 for
+    `--cpu-steps` RK3 steps (single-threaded C).  Also reports the GPU FP32/FP64 error
+    against the oracle on that same sample."""
+    import numpy as np
+
+    import oracle
+    from paper_1808_04960_gb300 import workloads
+    n = args.cpu_grid
+    U0, meta = workloads.isentropic_vortex(n)
+    o = oracle.Oracle(U0.shape[1:], meta["dx"], meta["bc"], R=args.R, ell_over_dx=12.0)
+    dt = 0.4 / o.max_rate(U0)
+    t0 = time.perf_counter()
+    ref = o.run(U0, dt, args.cpu_steps)
+    secs = time.perf_counter() - t0
+    out = {"value": n * n * 3 * args.cpu_steps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"vortex {n}x{n}, GP-R{args.R}, {args.cpu_steps} SSP-RK3 steps, FP64 C oracle, "
+                     f"1 thread, {secs:.2f} s"}
+    if gpu_compare:
+        import torch
+
+        from paper_1808_04960_gb300 import gpweno
+        errs = {}
+        for dtype in ("f32", "f64"):
+            tdt = torch.float32 if dtype == "f32" else torch.float64
+            plan = gpweno.Plan(args.R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
+            U = torch.from_numpy(U0).to("cuda", tdt).contiguous()
+            s = torch.empty((2,) + tuple(U.shape), dtype=tdt, device="cuda")
+            for _ in range(args.cpu_steps):
+                plan.rk3_step(U, s, dt=dt)
+            d = np.abs(U.double().cpu().numpy() - ref)
+            errs[dtype] = {"l1": float(d.mean()), "linf": float(d.max())}
+        out["gpu_error_vs_oracle_on_sample"] = errs
+    return out
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1808_04960_gb300 import workloads
+    n = args.cpu_grid
+    U0, meta = workloads.isentropic_vortex(n)
+    o = oracle.Oracle(U0.shape[1:], meta["dx"], meta["bc"], R=args.R, ell_over_dx=12.0)
+    dt = 0.4 / o.max_rate(U0)
+    U = U0
+    for _ in range(args.warmup):
+        U = o.rk3_step(U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = o.rk3_step(U, dt)
+    secs = time.perf_counter() - t0
+    v = n * n * 3 * args.steps / secs
+    sample = f"vortex {n}x{n} (bounded sample of the {args.grid}x{args.grid} workload), GP-R{args.R}, " \
+             f"1 SSP-RK3 step per bench step, FP64 C oracle, 1 thread"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"2D isentropic vortex {args.grid}x{args.grid} periodic [-5,5]^2, GP-R{args.R}, "
+                                   "l=12dx, sigma=3dx, SSP-RK3 fixed dt (CFL 0.4)", "grid": [args.grid, args.grid],
+                       "R": args.R, "sample_grid": [n, n]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpweno", choices=["gpweno", "reference"])
+    ap.add_argument("--grid", type=int, default=1024)
+    ap.add_argument("--R", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-grid", type=int, default=256)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtypes", default="f32,f64", help="comma list; f32 is always first and required")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
