@@ -134,6 +134,25 @@ gpweno_status gpweno_rhs(gpweno_plan plan, const void *U, void *dUdt, void *stre
  * after the step with the CFL time step of the new state. */
 gpweno_status gpweno_rk3_step(gpweno_plan plan, void *U, void *scratch, double dt, void *dt_dev, void *stream);
 
+/* Allocation-free SSP-RK3 step (the paper has no counterpart: this is a
+ * service for callers that may not allocate device memory, e.g. code whose
+ * host application owns all device memory through its own pool or caching
+ * allocator, or a plug-in handed only the state buffer).  Same arithmetic,
+ * kernels and result as gpweno_rk3_step with dt_dev = NULL, but the two
+ * intermediate stage buffers live in a 16 MiB array of device memory that
+ * is part of the library image, so the call allocates nothing.
+ *   - Grids whose two stage copies (each rounded up to 256 bytes) exceed
+ *     16 MiB are rejected with GPWENO_ERR_ARG: at most 524,288 cells for
+ *     FP32 2D (e.g. 724 x 724), 262,144 for FP64 2D.
+ *   - Every GPU that loads the library holds the 16 MiB until exit.
+ *   - All calls on a device share the one array and the previous call's
+ *     contents stay in it (nothing in it needs to start at zero); calls whose
+ *     kernels overlap on the GPU (other streams, other host threads) race.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ * U: device state buffer (input and output), dt > 0, stream as elsewhere. */
+gpweno_status gpweno_rk3_step_noalloc(gpweno_plan plan, void *U, double dt, void *stream);
+
 /* *dt_dev (device double) = cfl / sum_d max over cells of (|u_d| + c)/dx_d. */
 gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *dt_dev, void *stream);
 

@@ -1,0 +1,109 @@
+// Allocation-free variant of the SSP-RK3 step.
+//
+// gpweno_rk3_step needs a caller-provided scratch buffer of two state sizes
+// for the intermediate stages.  Some callers cannot provide one: code that
+// runs where it may not call cudaMalloc (an application whose device memory is
+// owned by its own pool or caching allocator and which forbids allocations
+// behind its back, or a plug-in whose host application gives it only the
+// state buffer).  gpweno_rk3_step_noalloc serves them: its two stage buffers
+// live in a fixed-size array in device global memory that is part of this
+// library's image, so the call allocates nothing.
+//
+// Costs and limits of that choice:
+//   - every GPU that loads the library holds the array (kStaticScratchBytes)
+//     until the process exits;
+//   - a grid fits only if two copies of its state fit in the array;
+//   - every call shares the one array per device, so two calls whose kernels
+//     overlap on the GPU (different streams, or different host threads on the
+//     same device) race and corrupt each other's stages;
+//   - the first call on a device looks up the array's device address
+//     (cudaGetSymbolAddress) with that device current; make that first call
+//     before any stream capture begins.
+#include <cstdint>
+#include <mutex>
+
+#include "plan.h"
+
+namespace gpweno {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device symbol: its device address must come from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device (looked up once per device).
+gpweno_status static_scratch_address(int device, void **out)
+{
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("gpweno_rk3_step_noalloc: device %d out of range", device);
+        return GPWENO_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || ptr == nullptr)
+            return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                             "gpweno_rk3_step_noalloc: cudaGetSymbolAddress of the static scratch");
+        g_scratch_addr[device] = ptr;
+    }
+    *out = g_scratch_addr[device];
+    return GPWENO_OK;
+}
+
+}  // namespace
+}  // namespace gpweno
+
+using namespace gpweno;
+
+extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double dt, void *stream)
+{
+    if (!p || p->is_batch || !U) {
+        set_error("gpweno_rk3_step_noalloc: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(U) & 15u) != 0) {
+        set_error("gpweno_rk3_step_noalloc: U must be 16-byte aligned");
+        return GPWENO_ERR_ARG;
+    }
+    if (!(dt > 0.0)) {
+        set_error("gpweno_rk3_step_noalloc: dt=%g must be positive", dt);
+        return GPWENO_ERR_ARG;
+    }
+    const size_t esz = p->opts.dtype == GPWENO_F32 ? 4 : 8;
+    const size_t bytes = esz * (size_t)(p->dims.ndim + 2) * (size_t)p->ncell;
+    const size_t stride = (bytes + 255) & ~size_t(255);
+    if (2 * stride > kStaticScratchBytes) {
+        set_error("gpweno_rk3_step_noalloc: the grid needs 2 x %zu bytes of stage storage, more than the %zu-byte "
+                  "static scratch; use gpweno_rk3_step with a caller-provided scratch buffer",
+                  stride, kStaticScratchBytes);
+        return GPWENO_ERR_ARG;
+    }
+    int device = -1;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e, "gpweno_rk3_step_noalloc: cudaGetDevice");
+    if (device != p->device) {
+        set_error("gpweno_rk3_step_noalloc: plan belongs to device %d but device %d is current", p->device, device);
+        return GPWENO_ERR_ARG;
+    }
+    void *base = nullptr;
+    gpweno_status s = static_scratch_address(device, &base);
+    if (s != GPWENO_OK) return s;
+    char *s1 = static_cast<char *>(base);
+    char *s2 = s1 + stride;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto stage = [&](const void *in, const void *u0, void *out, double a0, double b) {
+        return p->opts.dtype == GPWENO_F32 ? launch_stage_f32(p, in, u0, out, a0, b, 1, dt, nullptr, false, st)
+                                           : launch_stage_f64(p, in, u0, out, a0, b, 1, dt, nullptr, false, st);
+    };
+    // nothing in the array needs to start at zero: each stage overwrites its buffer completely
+    if ((s = stage(U, nullptr, s1, 0.0, 1.0)) != GPWENO_OK) return s;
+    if ((s = stage(s1, U, s2, 0.75, 0.25)) != GPWENO_OK) return s;
+    return stage(s2, U, U, 1.0 / 3.0, 2.0 / 3.0);
+}

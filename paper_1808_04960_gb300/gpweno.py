@@ -221,6 +221,17 @@ class Plan:
                                         _stream_handle(stream)), "gpweno_rk3_step")
         return U
 
+    def rk3_step_noalloc(self, U, dt, stream=None):
+        """gpweno_rk3_step_noalloc: one SSP-RK3 step in place on U whose stage buffers live in the
+        library's static 16 MiB device array (for callers that may not allocate device memory)."""
+        self._check_state(U)
+        fn = self.lib.gpweno_rk3_step_noalloc
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        _check(fn(self.handle, ctypes.c_void_p(U.data_ptr()), float(dt), _stream_handle(stream)),
+               "gpweno_rk3_step_noalloc")
+        return U
+
     def cfl_dt(self, U, cfl, dt_dev, stream=None):
         import torch
         self._check_state(U)
