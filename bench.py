@@ -208,7 +208,7 @@ def run_gpu(args):
     # accuracy of FP32 against the FP64 path after the same number of steps from the same data
     acc = None
     if "f64" in states:
-        n32 = args.warmup + (1 if args.graph else 0) + results["f32"]["steps"]
+        n32 = args.acc_steps
         p32, _, s32 = states["f32"]
         U32 = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
         U64 = torch.from_numpy(U0).to("cuda", torch.float64).contiguous()
@@ -314,13 +314,18 @@ def cpu_baseline(args, dt_full, gpu_compare=True):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, one SSP-RK3 step per bench step on a
+    bounded sample of the workload (a smaller vortex grid, sized so the whole run takes about two
+    minutes at ~3.5 us per cell and RHS evaluation)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     import oracle
     from paper_1808_04960_gb300 import workloads
-    n = args.cpu_grid
+    per_step_budget = 120.0 / (args.steps + args.warmup)
+    n = int(math.sqrt(per_step_budget / (3 * 3.5e-6)))
+    n = max(32, min(args.cpu_grid, (n // 8) * 8))
     U0, meta = workloads.isentropic_vortex(n)
     o = oracle.Oracle(U0.shape[1:], meta["dx"], meta["bc"], R=args.R, ell_over_dx=12.0)
     dt = 0.4 / o.max_rate(U0)
@@ -347,12 +352,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpweno", choices=["gpweno", "reference"])
     ap.add_argument("--grid", type=int, default=1024)
     ap.add_argument("--R", type=int, default=2)
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=60)
+    ap.add_argument("--acc-steps", type=int, default=100, help="steps of the FP32-vs-FP64 accuracy run")
     ap.add_argument("--cpu-grid", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-graph", dest="graph", action="store_false")

@@ -20,8 +20,9 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
         for (int j = 0; j < S; ++j) {
             t.wl[m][j] = (T)p->tab.wl[m * S + j];
             t.wr[m][j] = (T)p->tab.wr[m * S + j];
-            t.P[m][j] = (T)p->tab.P[m * S + j];
         }
+    for (int k = 0; k < S; ++k)
+        for (int j = 0; j < (R + 2) / 2; ++j) t.Ph[k][j] = (T)p->tab.Ph[k * S + j];
     for (int m = 0; m < S; ++m) {
         t.gl[m] = (T)p->tab.gl[m];
         t.gr[m] = (T)p->tab.gr[m];
@@ -32,32 +33,19 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
     return t;
 }
 
-// Choose the strip width and the number of row segments of the 2D kernel:
-// strips as wide as the block allows, then the segment count that minimises
-// (waves of CTAs) x (rows per segment + 5 warm-up y-face rows).
+// Schedule of the 2D kernel: strips as wide as the block allows (balanced
+// widths), one CTA per resident slot, each CTA an equal share of the strips'
+// rows (at least 8 rows, so the 5 warm-up y-face rows stay a minor cost).
 inline Schedule schedule2d(int nx, int ny, int nt, int slots)
 {
     Schedule s;
     const int wmax = nt - 5;
     s.nstrips = (nx + wmax - 1) / wmax;
     s.W = (nx + s.nstrips - 1) / s.nstrips;
-    double best = 1e300;
-    int best_seg = 1;
-    const int segmax = std::max(1, std::min(ny, 8 * slots));
-    for (int nseg = 1; nseg <= segmax; ++nseg) {
-        const int H = (ny + nseg - 1) / nseg;
-        const int items = s.nstrips * nseg;
-        const int waves = (items + slots - 1) / slots;
-        const double cost = (double)waves * (H + 5.5);
-        if (cost < best - 1e-9) {
-            best = cost;
-            best_seg = nseg;
-        }
-    }
-    s.nseg = best_seg;
-    s.H = (ny + best_seg - 1) / best_seg;
-    s.nseg = (ny + s.H - 1) / s.H;
-    s.grid = std::min(s.nstrips * s.nseg, slots);
+    const long long rows = (long long)s.nstrips * ny;
+    s.grid = (int)std::max(1LL, std::min<long long>(slots, rows / 8));
+    s.H = (int)((rows + s.grid - 1) / s.grid);
+    s.nseg = 0;
     return s;
 }
 

@@ -29,11 +29,29 @@ namespace gpweno {
 template <typename T>
 struct Num;
 
+// FP32: single-instruction approximations (PTX rcp/rsqrt/sqrt .approx.ftz,
+// about 1 ulp), enough for an FP32 path whose error budget is set by the
+// stored FP32 state.
 template <>
 struct Num<float> {
-    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
-    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float rsqrt(float x)
+    {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float sqrt(float x)
+    {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
     static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
     static __device__ __forceinline__ float fmax(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float fmin(float a, float b) { return fminf(a, b); }
@@ -58,7 +76,8 @@ struct FaceTables {
     T wr[R + 1][R + 1];   // sub-stencil weights, right state
     T gl[R + 1];          // linear weights, left state
     T gr[R + 1];          // linear weights, right state
-    T P[R + 1][R + 1];    // P_h = v_h / sqrt(lambda_h) of K_m(sigma)
+    T Ph[R + 1][(R + 2) / 2];  // P_h = v_h / sqrt(lambda_h) of K_m(sigma), half form, largest lambda first:
+                               // even rows symmetric, odd rows skew (K_m is persymmetric)
     T eps;                // WENO epsilon
     T gamma;              // ratio of specific heats
     int p;                // WENO power, 1 or 2
@@ -172,15 +191,37 @@ __device__ __forceinline__ bool face_flux(const T (&st)[2 * R + 2][NC], const Fa
             f[j] = v;
         }
         // --- smoothness indicators on the R+2 windows f[w..w+R] ----------
+        // beta = sum_h (P_h . f)^2 with P_h symmetric or skew: pair f_j with
+        // f_{S-1-j} once, then each dot product takes half the multiplies.
+        constexpr int S = R + 1, HALF = S / 2;
         T b[R + 2];
 #pragma unroll
         for (int w = 0; w < R + 2; ++w) {
+            T ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                ps[j] = f[w + j] + f[w + S - 1 - j];
+                ms[j] = f[w + j] - f[w + S - 1 - j];
+            }
             T beta = T(0);
 #pragma unroll
-            for (int h = 0; h <= R; ++h) {
-                T d = T(0);
+            for (int k = 0; k < S; ++k) {
+                T d;
+                if (k % 2 == 0) {
+                    if (S % 2 == 1) {
+                        d = tb.Ph[k][HALF] * f[w + HALF];
 #pragma unroll
-                for (int j = 0; j <= R; ++j) d = fma(tb.P[h][j], f[w + j], d);
+                        for (int j = 0; j < HALF; ++j) d = fma(tb.Ph[k][j], ps[j], d);
+                    } else {
+                        d = tb.Ph[k][0] * ps[0];
+#pragma unroll
+                        for (int j = 1; j < HALF; ++j) d = fma(tb.Ph[k][j], ps[j], d);
+                    }
+                } else {
+                    d = tb.Ph[k][0] * ms[0];
+#pragma unroll
+                    for (int j = 1; j < HALF; ++j) d = fma(tb.Ph[k][j], ms[j], d);
+                }
                 beta = fma(d, d, beta);
             }
             b[w] = tb.eps + beta;

@@ -372,6 +372,20 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
         dd rs = div(make(1.0), sqrt_dd(lam));
         for (int j = 0; j < S; ++j) out->P[h * S + j] = to_d(mul(V[j][e], rs));
     }
+    // half form, descending lambda, with the symmetric/skew alternation checked
+    for (int k = 0; k < S; ++k) {
+        const double *row = out->P + (S - 1 - k) * S;
+        double scale = 0.0;
+        for (int j = 0; j < S; ++j) scale = std::fmax(scale, std::fabs(row[j]));
+        const double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+        for (int j = 0; j < S; ++j)
+            if (std::fabs(row[j] - sgn * row[S - 1 - j]) > 1e-12 * scale) {
+                std::snprintf(err, errlen, "eigenvector %d of K_m(sigma) is not %s", k,
+                              k % 2 == 0 ? "symmetric" : "skew-symmetric");
+                return 2;
+            }
+        for (int j = 0; j < (S + 1) / 2; ++j) out->Ph[k * S + j] = row[j];
+    }
     return 0;
 }
 

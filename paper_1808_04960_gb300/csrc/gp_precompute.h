@@ -21,6 +21,13 @@ struct GpTables {
     // smoothness factors P[h][j] = v_h[j] / sqrt(lambda_h) of K_m(sigma), lambda ascending
     double P[kMaxS * kMaxS];
     double lambda[kMaxS];
+    // The same factors in half form, largest eigenvalue first: K_m(sigma) is
+    // symmetric Toeplitz, hence persymmetric, and the SE kernel is totally
+    // positive, so in descending order of lambda the eigenvectors alternate
+    // symmetric (k even: v_j = v_{S-1-j}) and skew (k odd: v_j = -v_{S-1-j}).
+    // Ph[k*S + j], j < (S+1)/2, holds the first half of P for the k-th largest
+    // eigenvalue; the precompute verifies the alternation.
+    double Ph[kMaxS * kMaxS];
     double ls_residual;          // ||M gamma - w||_2 of the left-state system
     double cond_estimate;        // rough condition estimate of K(l)
 };

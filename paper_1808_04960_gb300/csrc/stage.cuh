@@ -58,20 +58,16 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-__device__ __forceinline__ int pmod(int a, int m)
-{
-    int r = a % m;
-    return r < 0 ? r + m : r;
-}
-
 // Ring geometry of the 2D kernel for radius R and block size NT.
 template <int R, int NT>
 struct Ring2D {
     static constexpr int G = R + 3;                      // ghost layers
     static constexpr int LOW = R > 2 ? R : 2;            // rows below s still in use
-    static constexpr int ROWS = LOW + R + 3;             // rows s-LOW .. s+R+2 (one prefetched)
+    static constexpr int NEEDED = LOW + R + 3;           // rows s-LOW .. s+R+2 (one prefetched)
+    static constexpr int ROWS = NEEDED <= 8 ? 8 : 16;    // power of two: slot = row & (ROWS-1)
     static constexpr int STRIDE = NT - 5 + 2 * G;        // elements per ring row and component
     static constexpr int WMAX = NT - 5;
+    static __device__ __forceinline__ int slot(int g) { return g & (ROWS - 1); }
 };
 
 template <typename T, int R, int NT>
@@ -93,9 +89,10 @@ __device__ __forceinline__ void rates2d(const T (&u)[4], T gam, const T (&idx)[3
     ry = (Num<T>::fabs(vy) + c) * idx[1];
 }
 
+// One segment: rows [y0, y1) of strip `strip`.
 template <typename T, int R, int NT>
-__device__ __forceinline__ void stage2d_item(const StageArgs<T> &a, const FaceTables<T, R> &tb, int item, T *smem,
-                                             T dt, T &rmx, T &rmy, bool &ok)
+__device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, int strip, int y0,
+                                                int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok)
 {
     using RG = Ring2D<R, NT>;
     constexpr int G = RG::G, ROWS = RG::ROWS, STRIDE = RG::STRIDE;
@@ -106,18 +103,15 @@ __device__ __forceinline__ void stage2d_item(const StageArgs<T> &a, const FaceTa
     const int tid = threadIdx.x;
     const int nx = a.n[0], ny = a.n[1];
     const long plane = (long)nx * ny;
-    const int strip = item % a.nstrips, seg = item / a.nstrips;
     const int x0 = strip * a.W;
     const int Wc = min(a.W, nx - x0);
-    const int y0 = seg * a.H;
-    const int y1 = min(y0 + a.H, ny);
     const int s_begin = y0 - 3, s_end = y1 + 1;
     const int rowlen = Wc + 2 * G;
     const T idx[3] = {a.idx[0], a.idx[1], a.idx[2]};
 
     auto load_row = [&](int g) {
         const int gy = bc_map(g, ny, a.per[1]);
-        T *dst = ring + pmod(g, ROWS) * (NC * STRIDE);
+        T *dst = ring + RG::slot(g) * (NC * STRIDE);
         const T *src = a.U + (long)gy * nx;
         for (int col = tid; col < rowlen; col += NT) {
             const int gx = bc_map(x0 - G + col, nx, a.per[0]);
@@ -152,14 +146,14 @@ __device__ __forceinline__ void stage2d_item(const StageArgs<T> &a, const FaceTa
         T u0[NC];
         const bool need_u0 = out_row && col_ok && a.mode == 1 && a.a0 != T(0);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) u0[c] = need_u0 ? __ldg(a.U0 + c * plane + (long)r * nx + x0 + tid) : T(0);
+        for (int c = 0; c < NC; ++c) u0[c] = need_u0 ? a.U0[c * plane + (long)r * nx + x0 + tid] : T(0);
 
         // ---- y-face s+1/2 of column tid --------------------------------
         if (col_ok) {
             T st[NS][NC];
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                const T *row = ring + pmod(s - R + q, ROWS) * (NC * STRIDE) + G + tid;
+                const T *row = ring + RG::slot(s - R + q) * (NC * STRIDE) + G + tid;
                 st[q][0] = row[0];
                 st[q][1] = row[2 * STRIDE];   // normal momentum: rho v
                 st[q][2] = row[1 * STRIDE];   // tangential: rho u
@@ -178,7 +172,7 @@ __device__ __forceinline__ void stage2d_item(const StageArgs<T> &a, const FaceTa
         }
         // ---- x-faces of output row r ----------------------------------
         if (out_row && tid < Wc + 5) {
-            const T *row = ring + pmod(r, ROWS) * (NC * STRIDE) + tid;
+            const T *row = ring + RG::slot(r) * (NC * STRIDE) + tid;
             T st[NS][NC];
 #pragma unroll
             for (int q = 0; q < NS; ++q)
@@ -196,7 +190,7 @@ __device__ __forceinline__ void stage2d_item(const StageArgs<T> &a, const FaceTa
 #pragma unroll
             for (int c = 0; c < NC; ++c) fyc[c] = corrected<T>(Fy[0][c], Fy[1][c], Fy[2][c], Fy[3][c], Fy[4][c]);
             if (out_row) {
-                const T *urow = ring + pmod(r, ROWS) * (NC * STRIDE) + G + tid;
+                const T *urow = ring + RG::slot(r) * (NC * STRIDE) + G + tid;
                 T res[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -258,8 +252,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
     const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
     T rmx = T(0), rmy = T(0);
     bool ok = true;
-    const int items = a.nstrips * a.nseg;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) stage2d_item<T, R, NT>(a, tb, item, smem, dt, rmx, rmy, ok);
+    // Balanced persistent schedule: the strips' rows, laid end to end
+    // (strip-major), are split into gridDim.x equal ranges; a range that
+    // crosses a strip boundary becomes two segments.
+    const int ny = a.n[1];
+    const long long total = (long long)a.nstrips * ny;
+    long long u = total * blockIdx.x / gridDim.x;
+    const long long uend = total * (blockIdx.x + 1) / gridDim.x;
+    while (u < uend) {
+        const int strip = (int)(u / ny);
+        const int y0 = (int)(u - (long long)strip * ny);
+        const int y1 = (int)min((long long)ny, y0 + (uend - u));
+        stage2d_segment<T, R, NT>(a, tb, strip, y0, y1, smem, dt, rmx, rmy, ok);
+        u += y1 - y0;
+    }
     finish_block<T>(a, rmx, rmy, T(0), ok);
 }
 
