@@ -182,7 +182,7 @@ def run_gpu(args):
         tdt = torch.float32 if dtype == "f32" else torch.float64
         plan = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
         U = torch.from_numpy(U0).to("cuda", tdt).contiguous()
-        scratch = torch.empty((2,) + tuple(U.shape), dtype=tdt, device="cuda")
+        scratch = torch.zeros((4,) + tuple(U.shape), dtype=tdt, device="cuda")
         steps = args.steps if dtype == "f32" else max(3, min(args.steps, args.fp64_steps))
         for _ in range(args.warmup):
             plan.rk3_step(U, scratch, dt=dt, stream=stream)
@@ -304,7 +304,7 @@ def cpu_baseline(args, dt_full, gpu_compare=True):
             tdt = torch.float32 if dtype == "f32" else torch.float64
             plan = gpweno.Plan(args.R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
             U = torch.from_numpy(U0).to("cuda", tdt).contiguous()
-            s = torch.empty((2,) + tuple(U.shape), dtype=tdt, device="cuda")
+            s = torch.zeros((4,) + tuple(U.shape), dtype=tdt, device="cuda")
             for _ in range(args.cpu_steps):
                 plan.rk3_step(U, s, dt=dt)
             d = np.abs(U.double().cpu().numpy() - ref)

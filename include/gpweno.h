@@ -127,8 +127,15 @@ gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, 
 gpweno_status gpweno_rhs(gpweno_plan plan, const void *U, void *dUdt, void *stream);
 
 /* One SSP-RK3 step in place on U (three fused stage launches):
- *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U <- 1/3 U + 2/3 (U2 + dt L(U2)).
- * scratch: caller-owned device buffer of 2 state sizes (U1, U2).
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U <- 1/3 U + 2/3 (U2 + dt L(U2)),
+ * carried in the equivalent increment form D1 = dt L(U), D2 = 1/4 (D1 + dt L(U+D1)),
+ * U <- U + 2/3 (D2 + dt L(U+D2)), whose final sum is compensated (TwoSum): the
+ * rounding remainder of each step's update is kept and added to the next one, so
+ * FP32 state rounding does not accumulate over long runs.
+ * scratch: caller-owned device buffer of 4 state sizes: [0] increment D, [1] U+D1,
+ * [2] U+D2 (all three overwritten every step), [3] the compensation remainder,
+ * carried from step to step -- it must be ZERO whenever U is (re)initialised and
+ * left untouched between steps of one run.
  * dt_dev: NULL to use `dt`; otherwise a device double holding dt, read by
  * the kernels (graph-capturable), and, when the plan's cfl > 0, overwritten
  * after the step with the CFL time step of the new state. */
@@ -137,13 +144,14 @@ gpweno_status gpweno_rk3_step(gpweno_plan plan, void *U, void *scratch, double d
 /* Allocation-free SSP-RK3 step (the paper has no counterpart: this is a
  * service for callers that may not allocate device memory, e.g. code whose
  * host application owns all device memory through its own pool or caching
- * allocator, or a plug-in handed only the state buffer).  Same arithmetic,
- * kernels and result as gpweno_rk3_step with dt_dev = NULL, but the two
- * intermediate stage buffers live in a 16 MiB array of device memory that
- * is part of the library image, so the call allocates nothing.
- *   - Grids whose two stage copies (each rounded up to 256 bytes) exceed
- *     16 MiB are rejected with GPWENO_ERR_ARG: at most 524,288 cells for
- *     FP32 2D (e.g. 724 x 724), 262,144 for FP64 2D.
+ * allocator, or a plug-in handed only the state buffer).  Same kernels as
+ * gpweno_rk3_step with dt_dev = NULL, but the three intermediate stage
+ * buffers live in a 16 MiB array of device memory that is part of the
+ * library image, so the call allocates nothing; no compensation remainder
+ * is carried between calls (each call's final sum is rounded once).
+ *   - Grids whose three stage copies (each rounded up to 256 bytes) exceed
+ *     16 MiB are rejected with GPWENO_ERR_ARG: at most 349,520 cells for
+ *     FP32 2D (e.g. 591 x 591), 174,760 for FP64 2D.
  *   - Every GPU that loads the library holds the 16 MiB until exit.
  *   - All calls on a device share the one array and the previous call's
  *     contents stay in it (nothing in it needs to start at zero); calls whose

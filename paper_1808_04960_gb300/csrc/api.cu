@@ -211,14 +211,53 @@ gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, 
     return GPWENO_OK;
 }
 
-static gpweno_status launch_stage(gpweno_plan p, const void *U, const void *U0, void *out, double a0, double b,
-                                  int mode, double dt, const double *dt_dev, bool want_rate, cudaStream_t st)
+}  // extern "C"
+
+static gpweno_status launch_stage(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    return p->opts.dtype == GPWENO_F32 ? launch_stage_f32(p, U, U0, out, a0, b, mode, dt, dt_dev, want_rate, st)
-                                       : launch_stage_f64(p, U, U0, out, a0, b, mode, dt, dt_dev, want_rate, st);
+    return p->opts.dtype == GPWENO_F32 ? launch_stage_f32(p, io, st) : launch_stage_f64(p, io, st);
 }
 
+namespace gpweno {
+
+gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, void *lo, double dt,
+                           const double *dt_dev, bool want_rate, cudaStream_t st)
+{
+    gpweno_status s;
+    StageIO io;
+    io.dt = dt;
+    io.dt_dev = dt_dev;
+    // D_1 = dt L(U^n), V_1 = U^n + D_1
+    io.U = U;
+    io.U0 = U;
+    io.Dout = D;
+    io.Vout = V1;
+    io.b = 1.0;
+    io.mode = 1;
+    if ((s = launch_stage(p, io, st)) != GPWENO_OK) return s;
+    // D_2 = 1/4 (D_1 + dt L(V_1)), V_2 = U^n + D_2
+    io.U = V1;
+    io.Din = D;
+    io.Vout = V2;
+    io.b = 0.25;
+    if ((s = launch_stage(p, io, st)) != GPWENO_OK) return s;
+    // U^{n+1} = U^n + 2/3 (D_2 + dt L(V_2)), compensated with lo
+    io.U = V2;
+    io.Dout = nullptr;
+    io.Vout = nullptr;
+    io.out = U;
+    io.lo = lo;
+    io.b = 2.0 / 3.0;
+    io.mode = 2;
+    io.want_rate = want_rate;
+    return launch_stage(p, io, st);
+}
+
+}  // namespace gpweno
+
 static bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+extern "C" {
 
 gpweno_status gpweno_rhs(gpweno_plan p, const void *U, void *dUdt, void *stream)
 {
@@ -231,7 +270,11 @@ gpweno_status gpweno_rhs(gpweno_plan p, const void *U, void *dUdt, void *stream)
         set_error("gpweno_rhs: U and dUdt must be distinct 16-byte aligned buffers");
         return GPWENO_ERR_ARG;
     }
-    return launch_stage(p, U, nullptr, dUdt, 0.0, 1.0, 0, 0.0, nullptr, false, (cudaStream_t)stream);
+    StageIO io;
+    io.U = U;
+    io.out = dUdt;
+    io.mode = 0;
+    return launch_stage(p, io, (cudaStream_t)stream);
 }
 
 gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, void *dt_dev, void *stream)
@@ -252,14 +295,11 @@ gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t esz = p->opts.dtype == GPWENO_F32 ? 4 : 8;
     const size_t bytes = esz * (size_t)(p->dims.ndim + 2) * (size_t)p->ncell;
-    char *s1 = static_cast<char *>(scratch);
-    char *s2 = s1 + bytes;
+    char *base = static_cast<char *>(scratch);
     const double *dtp = static_cast<const double *>(dt_dev);
     const bool cfl = dt_dev && p->opts.cfl > 0.0;
-    gpweno_status s;
-    if ((s = launch_stage(p, U, nullptr, s1, 0.0, 1.0, 1, dt, dtp, false, st)) != GPWENO_OK) return s;
-    if ((s = launch_stage(p, s1, U, s2, 0.75, 0.25, 1, dt, dtp, false, st)) != GPWENO_OK) return s;
-    if ((s = launch_stage(p, s2, U, U, 1.0 / 3.0, 2.0 / 3.0, 1, dt, dtp, cfl, st)) != GPWENO_OK) return s;
+    gpweno_status s = rk3_sequence(p, U, base, base + bytes, base + 2 * bytes, base + 3 * bytes, dt, dtp, cfl, st);
+    if (s != GPWENO_OK) return s;
     if (cfl) {
         dt_from_rate_kernel<<<1, 32, 0, st>>>(p->ws, p->dims.ndim, p->opts.cfl, static_cast<double *>(dt_dev));
         GPW_CHECK(cudaGetLastError(), "dt kernel launch");

@@ -26,6 +26,9 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
     for (int m = 0; m < S; ++m) {
         t.gl[m] = (T)p->tab.gl[m];
         t.gr[m] = (T)p->tab.gr[m];
+        t.sl1[m] = (T)p->tab.sl1[m];
+        t.sr1[m] = (T)p->tab.sr1[m];
+        t.Psum[m] = (T)p->tab.Psum[m];
     }
     t.eps = (T)p->opts.eps;
     t.gamma = (T)p->gamma;
@@ -104,19 +107,22 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
 }
 
 template <typename T>
-gpweno_status launch_stage_T(gpweno_plan p, const void *U, const void *U0, void *out, double a0, double b, int mode,
-                             double dt, const double *dt_dev, bool want_rate, cudaStream_t st)
+gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
     StageArgs<T> a = base_args<T>(p);
-    a.U = static_cast<const T *>(U);
-    a.U0 = static_cast<const T *>(U0);
-    a.out = static_cast<T *>(out);
-    a.a0 = (T)a0;
-    a.b = (T)b;
-    a.mode = mode;
-    a.dt = dt;
-    a.dt_dev = dt_dev;
-    a.rate = want_rate ? p->ws : nullptr;
+    a.U = static_cast<const T *>(io.U);
+    a.U0 = static_cast<const T *>(io.U0);
+    a.Din = static_cast<const T *>(io.Din);
+    a.Dout = static_cast<T *>(io.Dout);
+    a.Vout = static_cast<T *>(io.Vout);
+    a.out = static_cast<T *>(io.out);
+    a.lo = static_cast<T *>(io.lo);
+    a.u0_is_stencil = io.U0 == io.U ? 1 : 0;
+    a.b = (T)io.b;
+    a.mode = io.mode;
+    a.dt = io.dt;
+    a.dt_dev = io.dt_dev;
+    a.rate = io.want_rate ? p->ws : nullptr;
     switch (p->R) {
     case 1: return launch_stage_R<T, 1>(p, a, st);
     case 2: return launch_stage_R<T, 2>(p, a, st);

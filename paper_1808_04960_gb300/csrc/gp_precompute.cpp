@@ -259,7 +259,7 @@ void jacobi(dd A[kMaxS][kMaxS], int n, dd V[kMaxS][kMaxS])
 // Linear weights for one prediction point: sub-stencil weights, full-stencil
 // weights, then least squares of M gamma = w through the normal equations.
 bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam, double *resid, double *cond,
-                 char *err, std::size_t errlen)
+                 double *sum1, char *err, std::size_t errlen)
 {
     const int S = R + 1, B = 2 * R + 1;
     int big2[kMaxBig];
@@ -312,6 +312,11 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
         for (int j = 0; j < S; ++j) w_sub[m * S + j] = to_d(ws[m][j]);
     for (int j = 0; j < B; ++j) w_big[j] = to_d(wb[j]);
     for (int m = 0; m < S; ++m) gam[m] = to_d(g[m]);
+    for (int m = 0; m < S; ++m) {
+        dd acc = make(-1.0);
+        for (int j = 0; j < S; ++j) acc = add(acc, ws[m][j]);
+        sum1[m] = to_d(acc);
+    }
     return true;
 }
 
@@ -338,8 +343,9 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
     dd ql = exp_dd(neg(div(make(1.0), mul_d(mul(make(ell), make(ell)), 8.0))));
     dd qs = exp_dd(neg(div(make(1.0), mul_d(mul(make(sigma), make(sigma)), 8.0))));
     double cond = 0.0, resid_r = 0.0;
-    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, err, errlen)) return 2;
-    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, err, errlen)) return 2;
+    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, out->sl1, err, errlen))
+        return 2;
+    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen)) return 2;
     out->cond_estimate = cond;
     // double-double carries ~2^-104 relative; demand cond * 2^-104 < 1e-6
     if (cond * 4.93e-32 > 1e-6) {
@@ -385,6 +391,9 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
                 return 2;
             }
         for (int j = 0; j < (S + 1) / 2; ++j) out->Ph[k * S + j] = row[j];
+        dd sum = make(0.0);
+        for (int j = 0; j < S; ++j) sum = add(sum, make(row[j]));
+        out->Psum[k] = (k % 2 == 0) ? to_d(sum) : 0.0;
     }
     return 0;
 }

@@ -28,6 +28,9 @@ struct GpTables {
     // Ph[k*S + j], j < (S+1)/2, holds the first half of P for the k-th largest
     // eigenvalue; the precompute verifies the alternation.
     double Ph[kMaxS * kMaxS];
+    double Psum[kMaxS];          // sum_j P_kj of each full row, same order as Ph (0 for skew rows)
+    double sl1[kMaxS];           // sum_j wl[m][j] - 1, from the double-double weights
+    double sr1[kMaxS];           // sum_j wr[m][j] - 1
     double ls_residual;          // ||M gamma - w||_2 of the left-state system
     double cond_estimate;        // rough condition estimate of K(l)
 };

@@ -1,18 +1,21 @@
 // Allocation-free variant of the SSP-RK3 step.
 //
-// gpweno_rk3_step needs a caller-provided scratch buffer of two state sizes
-// for the intermediate stages.  Some callers cannot provide one: code that
+// gpweno_rk3_step needs a caller-provided scratch buffer of four state sizes
+// for the intermediate stages and the compensation remainder.  Some callers cannot provide one: code that
 // runs where it may not call cudaMalloc (an application whose device memory is
 // owned by its own pool or caching allocator and which forbids allocations
 // behind its back, or a plug-in whose host application gives it only the
-// state buffer).  gpweno_rk3_step_noalloc serves them: its two stage buffers
+// state buffer).  gpweno_rk3_step_noalloc serves them: its three stage buffers
 // live in a fixed-size array in device global memory that is part of this
 // library's image, so the call allocates nothing.
 //
 // Costs and limits of that choice:
 //   - every GPU that loads the library holds the array (kStaticScratchBytes)
 //     until the process exits;
-//   - a grid fits only if two copies of its state fit in the array;
+//   - a grid fits only if three copies of its state fit in the array;
+//   - unlike gpweno_rk3_step, no compensation remainder is carried from one
+//     call to the next (there is nowhere private to keep it), so long FP32
+//     runs accumulate state rounding as an uncompensated sum would;
 //   - every call shares the one array per device, so two calls whose kernels
 //     overlap on the GPU (different streams, or different host threads on the
 //     same device) race and corrupt each other's stages;
@@ -79,8 +82,8 @@ extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double 
     const size_t esz = p->opts.dtype == GPWENO_F32 ? 4 : 8;
     const size_t bytes = esz * (size_t)(p->dims.ndim + 2) * (size_t)p->ncell;
     const size_t stride = (bytes + 255) & ~size_t(255);
-    if (2 * stride > kStaticScratchBytes) {
-        set_error("gpweno_rk3_step_noalloc: the grid needs 2 x %zu bytes of stage storage, more than the %zu-byte "
+    if (3 * stride > kStaticScratchBytes) {
+        set_error("gpweno_rk3_step_noalloc: the grid needs 3 x %zu bytes of stage storage, more than the %zu-byte "
                   "static scratch; use gpweno_rk3_step with a caller-provided scratch buffer",
                   stride, kStaticScratchBytes);
         return GPWENO_ERR_ARG;
@@ -95,15 +98,9 @@ extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double 
     void *base = nullptr;
     gpweno_status s = static_scratch_address(device, &base);
     if (s != GPWENO_OK) return s;
-    char *s1 = static_cast<char *>(base);
-    char *s2 = s1 + stride;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    auto stage = [&](const void *in, const void *u0, void *out, double a0, double b) {
-        return p->opts.dtype == GPWENO_F32 ? launch_stage_f32(p, in, u0, out, a0, b, 1, dt, nullptr, false, st)
-                                           : launch_stage_f64(p, in, u0, out, a0, b, 1, dt, nullptr, false, st);
-    };
-    // nothing in the array needs to start at zero: each stage overwrites its buffer completely
-    if ((s = stage(U, nullptr, s1, 0.0, 1.0)) != GPWENO_OK) return s;
-    if ((s = stage(s1, U, s2, 0.75, 0.25)) != GPWENO_OK) return s;
-    return stage(s2, U, U, 1.0 / 3.0, 2.0 / 3.0);
+    char *s0 = static_cast<char *>(base);
+    // nothing in the array needs to start at zero: each stage overwrites its buffers
+    // completely, and no compensation remainder is carried between calls
+    return rk3_sequence(p, U, s0, s0 + stride, s0 + 2 * stride, nullptr, dt, nullptr, false,
+                        static_cast<cudaStream_t>(stream));
 }

@@ -26,16 +26,30 @@
 
 namespace gpweno {
 
+// Stage modes.  The SSP-RK3 step is carried in increment form,
+//   D_1 = dt L(U^n),  D_2 = 1/4 (D_1 + dt L(U^n + D_1)),  D_3 = 2/3 (D_2 + dt L(U^n + D_2)),
+//   U^{n+1} = U^n + D_3,
+// which is the Shu-Osher form rewritten with U^(k) = U^n + D_k: increments are
+// stored with their own relative precision, and the final sum is compensated
+// (TwoSum) with a running remainder `lo`, so state rounding does not
+// accumulate over many steps.
+enum StageMode { kModeRHS = 0, kModeIncrement = 1, kModeFinal = 2 };
+
 template <typename T>
 struct StageArgs {
-    const T *U;                // stage input (stencil) state, SoA [nc][nz][ny][nx]
-    const T *U0;               // U^n for the stage combination (unused if a0 == 0 or mode == 0)
-    T *out;                    // result
+    const T *U;                // stencil state of this stage, SoA [nc][nz][ny][nx]
+    const T *U0;               // U^n at the output cell (modes 1, 2); may equal U
+    const T *Din;              // previous increment at the output cell (null = 0)
+    T *Dout;                   // mode 1: D_k = b (Din + dt L); may equal Din
+    T *Vout;                   // mode 1: U^n + D_k (next stage's stencil state)
+    T *out;                    // mode 0: L(U); mode 2: U^{n+1} (may equal U0)
+    T *lo;                     // mode 2: compensation remainder in/out (null: none)
     int n[3];                  // cells per dimension (x, y, z)
     int per[3];                // periodic flag per dimension
     T idx[3];                  // 1/dx per dimension
-    T a0, b;                   // stage: out = a0 U0 + b (U + dt L(U))
-    int mode;                  // 0: out = L(U); 1: stage combination
+    T b;                       // stage weight b_k
+    int mode;                  // StageMode
+    int u0_is_stencil;         // U0 == U: take U^n from the staged stencil data
     const double *dt_dev;      // device dt (or null: use dt)
     double dt;
     unsigned long long *rate;  // if non-null: atomic max of (|u_d| + c)/dx_d of the result (double bits)
@@ -74,7 +88,46 @@ template <typename T, int R, int NT>
 constexpr size_t stage2d_smem_bytes()
 {
     using RG = Ring2D<R, NT>;
-    return sizeof(T) * (size_t)(RG::ROWS * 4 * RG::STRIDE + 4 * NT);
+    return sizeof(T) * (size_t)(RG::ROWS * 4 * RG::STRIDE + 2 * 4 * NT);
+}
+
+// Error-free sum a + b = s + e (Knuth's TwoSum).
+template <typename T>
+__device__ __forceinline__ T two_sum(T a, T b, T &e)
+{
+    const T s = a + b;
+    const T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// Epilogue of one cell and component: L is the RHS, u the stencil-state value of
+// the cell, u0/din/lo the prefetched U^n, previous increment and remainder.
+// Returns the value whose wavespeed the CFL reduction sees (mode 2: U^{n+1}).
+template <typename T>
+__device__ __forceinline__ T stage_epilogue(const StageArgs<T> &a, long cell, T L, T u0, T din, T lo, T dt)
+{
+    if (a.mode == kModeRHS) {
+        a.out[cell] = L;
+        return L;
+    }
+    const T inc = a.b * fma(dt, L, din);
+    if (a.mode == kModeIncrement) {
+        a.Dout[cell] = inc;
+        a.Vout[cell] = u0 + inc;
+        return u0 + inc;
+    }
+    if (a.lo) {
+        T e;
+        const T t = inc + lo;
+        const T snew = two_sum<T>(u0, t, e);
+        a.out[cell] = snew;
+        a.lo[cell] = e;
+        return snew;
+    }
+    const T snew = u0 + inc;
+    a.out[cell] = snew;
+    return snew;
 }
 
 // Rate (|u_d| + c) / dx_d of a natural-order 2D state.
@@ -99,7 +152,8 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     constexpr int NC = 4;
     constexpr int NS = 2 * R + 2;
     T *ring = smem;                              // [ROWS][NC][STRIDE]
-    T *Fx = smem + ROWS * NC * STRIDE;           // [NC][NT]
+    T *FA = smem + ROWS * NC * STRIDE;           // [NC][NT]  x-face A = F_{s+1/2} - F(U_s)
+    T *FB = FA + NC * NT;                        // [NC][NT]  x-face B = F(U_{s+1}) - F(U_s)
     const int tid = threadIdx.x;
     const int nx = a.n[0], ny = a.n[1];
     const long plane = (long)nx * ny;
@@ -126,14 +180,15 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     cp_async_wait_all();
     __syncthreads();
 
-    T Fy[5][NC];
-    T fy_prev[NC];
+    // per column: flux jumps dF_{s'} = F_{s'+1/2} - F_{s'-1/2} across the last five rows,
+    // and A, B of the previous y-face
+    T Dy[5][NC], Ap[NC], Bp[NC];
 #pragma unroll
     for (int k = 0; k < 5; ++k)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) Fy[k][c] = T(0);
+        for (int c = 0; c < NC; ++c) Dy[k][c] = T(0);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) fy_prev[c] = T(0);
+    for (int c = 0; c < NC; ++c) Ap[c] = Bp[c] = T(0);
 
     for (int s = s_begin; s <= s_end; ++s) {
         if (s < s_end) load_row(s + 2 + R);
@@ -142,11 +197,17 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         const bool out_row = r >= y0;
         const bool col_ok = tid < Wc;
 
-        // U^n of this thread's output cell, in flight during the face work
-        T u0[NC];
-        const bool need_u0 = out_row && col_ok && a.mode == 1 && a.a0 != T(0);
+        // U^n, previous increment and remainder of this thread's output cell,
+        // in flight during the face work
+        T u0[NC], din[NC], lov[NC];
+        const long cell = (long)r * nx + x0 + tid;
+        const bool epi = out_row && col_ok && a.mode != kModeRHS;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) u0[c] = need_u0 ? a.U0[c * plane + (long)r * nx + x0 + tid] : T(0);
+        for (int c = 0; c < NC; ++c) {
+            u0[c] = (epi && !a.u0_is_stencil) ? a.U0[c * plane + cell] : T(0);
+            din[c] = (epi && a.Din) ? a.Din[c * plane + cell] : T(0);
+            lov[c] = (epi && a.lo && a.mode == kModeFinal) ? a.lo[c * plane + cell] : T(0);
+        }
 
         // ---- y-face s+1/2 of column tid --------------------------------
         if (col_ok) {
@@ -159,16 +220,20 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 st[q][2] = row[1 * STRIDE];   // tangential: rho u
                 st[q][3] = row[3 * STRIDE];
             }
-            T F[NC];
-            ok = face_flux<T, NC, R>(st, tb, F) && ok;
+            T An[NC], Bn[NC];
+            ok = face_rel<T, NC, R>(st, tb, An, Bn) && ok;
+            const T Ac[NC] = {An[0], An[2], An[1], An[3]};   // back to (rho, rho u, rho v, E)
+            const T Bc[NC] = {Bn[0], Bn[2], Bn[1], Bn[3]};
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) Fy[k][c] = Fy[k + 1][c];
-            Fy[4][0] = F[0];
-            Fy[4][1] = F[2];
-            Fy[4][2] = F[1];
-            Fy[4][3] = F[3];
+                for (int c = 0; c < NC; ++c) Dy[k][c] = Dy[k + 1][c];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                Dy[4][c] = Ac[c] - Ap[c] + Bp[c];   // jump across row s (valid once s > s_begin)
+                Ap[c] = Ac[c];
+                Bp[c] = Bc[c];
+            }
         }
         // ---- x-faces of output row r ----------------------------------
         if (out_row && tid < Wc + 5) {
@@ -178,45 +243,39 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             for (int q = 0; q < NS; ++q)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + q];
-            T F[NC];
-            ok = face_flux<T, NC, R>(st, tb, F) && ok;
+            T An[NC], Bn[NC];
+            ok = face_rel<T, NC, R>(st, tb, An, Bn) && ok;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) Fx[c * NT + tid] = F[c];
+            for (int c = 0; c < NC; ++c) {
+                FA[c * NT + tid] = An[c];
+                FB[c * NT + tid] = Bn[c];
+            }
         }
         __syncthreads();
-        // ---- correction, divergence, stage combination ----------------
-        if (s >= s_begin + 4 && col_ok) {
-            T fyc[NC];
+        // ---- divergence and stage combination -------------------------
+        if (out_row && col_ok) {
+            const T *urow = ring + RG::slot(r) * (NC * STRIDE) + G + tid;
+            T res[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) fyc[c] = corrected<T>(Fy[0][c], Fy[1][c], Fy[2][c], Fy[3][c], Fy[4][c]);
-            if (out_row) {
-                const T *urow = ring + RG::slot(r) * (NC * STRIDE) + G + tid;
-                T res[NC];
+            for (int c = 0; c < NC; ++c) {
+                // x-faces t = tid..tid+5 are s' = x-3..x+2 around cell x = x0 + tid
+                const T *fa = FA + c * NT + tid;
+                const T *fb = FB + c * NT + tid;
+                T dx[5];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const T *fx = Fx + c * NT + tid;
-                    const T fxp = corrected<T>(fx[1], fx[2], fx[3], fx[4], fx[5]);
-                    const T fxm = corrected<T>(fx[0], fx[1], fx[2], fx[3], fx[4]);
-                    const T L = -(fxp - fxm) * idx[0] - (fyc[c] - fy_prev[c]) * idx[1];
-                    if (a.mode == 0) {
-                        res[c] = L;
-                    } else {
-                        const T v = fma(dt, L, urow[c * STRIDE]);
-                        res[c] = a.a0 != T(0) ? fma(a.a0, u0[c], a.b * v) : a.b * v;
-                    }
-                }
-                T *o = a.out + (long)r * nx + x0 + tid;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) o[c * plane] = res[c];
-                if (a.rate) {
-                    T rx, ry;
-                    rates2d<T>(res, tb.gamma, idx, rx, ry);
-                    rmx = Num<T>::fmax(rmx, rx);
-                    rmy = Num<T>::fmax(rmy, ry);
-                }
+                for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
+                const T divx = corrected_divergence<T>(dx[0], dx[1], dx[2], dx[3], dx[4]);
+                const T divy = corrected_divergence<T>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
+                const T L = -fma(divx, idx[0], divy * idx[1]);
+                const T un = a.u0_is_stencil ? urow[c * STRIDE] : u0[c];
+                res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt);
             }
-#pragma unroll
-            for (int c = 0; c < NC; ++c) fy_prev[c] = fyc[c];
+            if (a.rate && a.mode == kModeFinal) {
+                T rx, ry;
+                rates2d<T>(res, tb.gamma, idx, rx, ry);
+                rmx = Num<T>::fmax(rmx, rx);
+                rmy = Num<T>::fmax(rmy, ry);
+            }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -276,7 +335,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
 template <typename T, int R, int NT>
 constexpr size_t stage1d_smem_bytes()
 {
-    return sizeof(T) * (size_t)(3 * (NT - 5 + 2 * (R + 3)) + 3 * NT);
+    return sizeof(T) * (size_t)(3 * (NT - 5 + 2 * (R + 3)) + 2 * 3 * NT);
 }
 
 template <typename T, int R, int NT>
@@ -286,7 +345,8 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<
     constexpr int STRIDE = NT - 5 + 2 * G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *row = reinterpret_cast<T *>(smem_raw);  // [NC][STRIDE]
-    T *Fx = row + NC * STRIDE;                 // [NC][NT]
+    T *FA = row + NC * STRIDE;                 // [NC][NT]
+    T *FB = FA + NC * NT;                      // [NC][NT]
     const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
     const int tid = threadIdx.x;
     const int nx = a.n[0];
@@ -307,29 +367,33 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<
             for (int q = 0; q < NS; ++q)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + tid + q];
-            T F[NC];
-            ok = face_flux<T, NC, R>(st, tb, F) && ok;
+            T An[NC], Bn[NC];
+            ok = face_rel<T, NC, R>(st, tb, An, Bn) && ok;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) Fx[c * NT + tid] = F[c];
+            for (int c = 0; c < NC; ++c) {
+                FA[c * NT + tid] = An[c];
+                FB[c * NT + tid] = Bn[c];
+            }
         }
         __syncthreads();
         if (tid < Wc) {
             T res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const T *fx = Fx + c * NT + tid;
-                const T L = -(corrected<T>(fx[1], fx[2], fx[3], fx[4], fx[5]) -
-                              corrected<T>(fx[0], fx[1], fx[2], fx[3], fx[4])) * a.idx[0];
-                if (a.mode == 0) {
-                    res[c] = L;
-                } else {
-                    const T v = fma(dt, L, row[c * STRIDE + G + tid]);
-                    res[c] = a.a0 != T(0) ? fma(a.a0, a.U0[(long)c * nx + x0 + tid], a.b * v) : a.b * v;
-                }
-            }
+                const T *fa = FA + c * NT + tid;
+                const T *fb = FB + c * NT + tid;
+                T dx[5];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) a.out[(long)c * nx + x0 + tid] = res[c];
-            if (a.rate) {
+                for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
+                const T L = -corrected_divergence<T>(dx[0], dx[1], dx[2], dx[3], dx[4]) * a.idx[0];
+                const long cell = (long)c * nx + x0 + tid;
+                const bool epi = a.mode != kModeRHS;
+                const T u0 = a.u0_is_stencil ? row[c * STRIDE + G + tid] : (epi ? a.U0[cell] : T(0));
+                const T din = (epi && a.Din) ? a.Din[cell] : T(0);
+                const T lov = (epi && a.lo && a.mode == kModeFinal) ? a.lo[cell] : T(0);
+                res[c] = stage_epilogue<T>(a, cell, L, u0, din, lov, dt);
+            }
+            if (a.rate && a.mode == kModeFinal) {
                 T ir = Num<T>::rcp(res[0]);
                 T vx = res[1] * ir;
                 T pr = (tb.gamma - T(1)) * (res[2] - T(0.5) * res[1] * vx);

@@ -6,10 +6,9 @@
 
 namespace gpweno {
 
-gpweno_status launch_stage_f64(gpweno_plan p, const void *U, const void *U0, void *out, double a0, double b, int mode,
-                               double dt, const double *dt_dev, bool want_rate, cudaStream_t st)
+gpweno_status launch_stage_f64(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    return launch_stage_T<double>(p, U, U0, out, a0, b, mode, dt, dt_dev, want_rate, st);
+    return launch_stage_T<double>(p, io, st);
 }
 
 gpweno_status launch_max_rate_f64(gpweno_plan p, const void *U, cudaStream_t st)

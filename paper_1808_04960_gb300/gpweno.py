@@ -184,6 +184,11 @@ class Plan:
         import torch
         return torch.empty((n, self.nc) + self.shape, dtype=self.dtype, device="cuda")
 
+    def new_scratch(self):
+        """Zeroed RK3 scratch of 4 state sizes (the last one is the compensation remainder)."""
+        import torch
+        return torch.zeros((4, self.nc) + self.shape, dtype=self.dtype, device="cuda")
+
     def tables(self) -> dict:
         import numpy as np
         S = self.R + 1
@@ -204,13 +209,15 @@ class Plan:
         return out
 
     def rk3_step(self, U, scratch, dt=0.0, dt_dev=None, stream=None):
-        """One SSP-RK3 step in place on U.  scratch: tensor of shape (2, nc, ...) of the plan's dtype.
+        """One SSP-RK3 step in place on U.  scratch: tensor of shape (4, nc, ...) of the plan's dtype
+        (see new_scratch); its last slice carries the compensation remainder between steps and must
+        be zero when U is (re)initialised.
         dt_dev: optional CUDA float64 scalar tensor holding dt (updated with the CFL dt if cfl > 0)."""
         import torch
         self._check_state(U)
-        if (scratch.dtype != self.dtype or tuple(scratch.shape) != (2, self.nc) + self.shape
+        if (scratch.dtype != self.dtype or tuple(scratch.shape) != (4, self.nc) + self.shape
                 or not scratch.is_contiguous() or not scratch.is_cuda):
-            raise ValueError("scratch must be a contiguous CUDA tensor of shape (2, nc, ...) and the plan's dtype")
+            raise ValueError("scratch must be a contiguous CUDA tensor of shape (4, nc, ...) and the plan's dtype")
         dptr = None
         if dt_dev is not None:
             if dt_dev.dtype != torch.float64 or not dt_dev.is_cuda or dt_dev.numel() != 1:
@@ -277,7 +284,7 @@ class BatchPlan:
             raise ValueError("one state and one scratch tensor per instance")
         for p, U, s in zip(self.plans, Us, scratches):
             p._check_state(U)
-            if tuple(s.shape) != (2, p.nc) + p.shape or s.dtype != p.dtype or not s.is_contiguous():
+            if tuple(s.shape) != (4, p.nc) + p.shape or s.dtype != p.dtype or not s.is_contiguous():
                 raise ValueError("bad scratch tensor")
         if dt_dev.dtype != torch.float64 or dt_dev.numel() != n or not dt_dev.is_cuda:
             raise ValueError("dt_dev must be a CUDA float64 tensor with one entry per instance")

@@ -51,7 +51,7 @@ def gpu_run(U, meta, R, dt, nsteps, dtype="f64", ell=12.0, sigma=3.0):
     plan = gpweno.Plan(R, ell, U.shape[1:], meta["dx"], meta["bc"], gamma=meta["gamma"], sigma_over_dx=sigma,
                        dtype=dtype)
     Ud = to_dev(U, dtype)
-    scratch = torch.empty((2,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
+    scratch = torch.zeros((4,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
     for _ in range(nsteps):
         plan.rk3_step(Ud, scratch, dt=dt)
     out = to_np(Ud)
@@ -198,7 +198,7 @@ def test_cfl_dt_and_fused_rate():
     plan.cfl_dt(Ud, 0.4, dt_dev)
     dt0 = float(dt_dev.item())
     assert abs(dt0 - o.cfl_dt(U, 0.4)) <= 1e-14 * dt0
-    scratch = torch.empty((2,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
+    scratch = torch.zeros((4,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
     plan.rk3_step(Ud, scratch, dt_dev=dt_dev)   # uses dt0, writes the next dt
     U1 = o.rk3_step(U, dt0)
     assert np.abs(to_np(Ud) - U1).mean() <= 1e-9
@@ -220,7 +220,7 @@ def test_launch_count():
     U, meta = W.isentropic_vortex(32)
     plan = gpweno.Plan(2, 12.0, U.shape[1:], meta["dx"], meta["bc"], dtype="f32", cfl=0.4)
     Ud = to_dev(U, "f32")
-    scratch = torch.empty((2,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
+    scratch = torch.zeros((4,) + tuple(Ud.shape), dtype=Ud.dtype, device="cuda")
     dt_dev = torch.full((1,), 0.01, dtype=torch.float64, device="cuda")
     plan.rk3_step(Ud, scratch, dt_dev=dt_dev)
     assert gpweno.last_launch_count() == 4

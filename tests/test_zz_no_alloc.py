@@ -39,7 +39,7 @@ def test_noalloc_matches_scratch_step(dtype, shape, tol):
     tdt = torch.float32 if dtype == "f32" else torch.float64
     Ua = torch.from_numpy(U0).to("cuda", tdt).contiguous()
     Ub = Ua.clone()
-    scratch = torch.empty((2,) + tuple(Ua.shape), dtype=tdt, device="cuda")
+    scratch = torch.zeros((4,) + tuple(Ua.shape), dtype=tdt, device="cuda")
     dt = 0.2 * min(meta["dx"])
     for call in range(2):
         plan.rk3_step(Ua, scratch, dt=dt)
@@ -53,7 +53,7 @@ def test_noalloc_matches_scratch_step(dtype, shape, tol):
 
 def test_noalloc_rejects_grids_beyond_the_static_array():
     import torch
-    U0, meta = W.isentropic_vortex(1024)       # 2 x 16 MiB of FP32 stages > 16 MiB
+    U0, meta = W.isentropic_vortex(1024)       # 3 x 16 MiB of FP32 stages > 16 MiB
     plan = gpweno.Plan(2, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype="f32")
     U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
     before = U.clone()
