@@ -12,8 +12,9 @@ Parity status per function (pins are in ``tests/test_oracle_*.py``):
                             eigen form, moment defects, linear-weight consistency)
   euler_oracle gp_weno      pinned (equal beta => omega = gamma, step data,
                             scaling, mirror symmetry)
-  euler_oracle roe/flux     pinned (L R = I, R diag(lambda) L = Jacobian,
-                            Roe property)
+  euler_oracle roe/flux     pinned (Roe property of the averaged state with a
+                            test-side conservative Jacobian; L R = I and
+                            R diag(lambda) L = primitive Jacobian)
   corrected_flux            pinned (exact for degree-5 flux primitives)
   oracle_rhs / rk3          pinned (free-stream preservation, conservation,
                             mirror and rotation symmetry, smooth-vortex order)
@@ -71,7 +72,7 @@ def _load():
             lib.oracle_max_rate.restype = ctypes.c_double
             lib.oracle_face.argtypes = [P, ctypes.c_int, dp, dp, dp, dp]
             lib.oracle_face.restype = ctypes.c_int
-            lib.oracle_roe.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
+            lib.oracle_roe.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp]
             lib.oracle_roe.restype = ctypes.c_int
             lib.oracle_gp_weno.argtypes = [P, dp, ctypes.c_int]
             lib.oracle_gp_weno.restype = ctypes.c_double
@@ -174,16 +175,18 @@ class Oracle:
 
 
 def roe_eigensystem(uL, uR, gamma=1.4):
-    """(Rm, Lm) at the Roe average of two conserved states given normal-first."""
+    """Roe average (rho, u..., H, c) of two conserved normal-first states and the
+    primitive-variable eigenvectors (Rm columns, Lm rows) at it."""
     lib = _load()
     uL = np.ascontiguousarray(uL, dtype=np.float64)
     uR = np.ascontiguousarray(uR, dtype=np.float64)
     nc = uL.shape[0]
+    roe = np.zeros(nc + 1)
     Rm = np.zeros((nc, nc))
     Lm = np.zeros((nc, nc))
-    if not lib.oracle_roe(nc, float(gamma), _ptr(uL), _ptr(uR), _ptr(Rm), _ptr(Lm)):
+    if not lib.oracle_roe(nc, float(gamma), _ptr(uL), _ptr(uR), _ptr(roe), _ptr(Rm), _ptr(Lm)):
         raise FloatingPointError("non-physical Roe state")
-    return Rm, Lm
+    return roe, Rm, Lm
 
 
 def corrected_flux(F5):

@@ -9,8 +9,8 @@
  *   - conserved variables and fluxes of the Euler equations (Eq. euler), ideal
  *     gas p = (gamma-1)(E - rho|u|^2/2);
  *   - Riemann states U^L, U^R at every face by GP-WENO interpolation of the
- *     characteristic variables (Section 3.2-3.3; Section 6 for the use of
- *     characteristic variables): candidate predictions q^m = w_m^T f_m
+ *     characteristic variables of the primitive variables (Section 3.2-3.3;
+ *     Section 6 for the use of characteristic variables): candidate predictions q^m = w_m^T f_m
  *     (Eq. candidate_interp), smoothness indicators beta_m = f_m^T K_m^{-1} f_m
  *     (Eq. gp-smooth, the definition form), WENO-JS weights
  *     omega_m = gamma_m/(eps+beta_m)^p normalised (Eq. weights), combination
@@ -23,9 +23,11 @@
  *   - the semi-discrete divergence (Eq. disc_fd) and the three-stage SSP-RK
  *     update in Shu-Osher form (Section 2, step 5).
  *
- * Readings where the paper is silent: characteristic projection with the
- * eigenvectors of the Roe-averaged state of the two cells sharing the face,
- * in the textbook basis written out in roe_eigensystem() below; local
+ * Readings where the paper is silent: the interpolated variables are the
+ * characteristic variables of the primitive system (rho, u, p), "FD-Primitive"
+ * (Section 1) with the projection of Section 6, using the eigenvectors of the
+ * primitive-variable Jacobian at the Roe average of the two cells sharing the
+ * face, in the basis written out in prim_eigensystem() below; local
  * Lax-Friedrichs speed max(|u_n|+c) over U^L and U^R; ghost cells by periodic
  * wrap or zero-gradient copy, G = R+3 layers (R+1 for the face stencil, two
  * more for the correction).
@@ -98,59 +100,77 @@ static void normal_flux(const double *u, int nc, double g, double *f)
     f[nc - 1] = un * (u[nc - 1] + p);
 }
 
-/* Right (columns of Rm) and left (rows of Lm) eigenvectors of the flux Jacobian
- * in the normal direction at the Roe average of uL and uR (normal-first
- * ordering).  Textbook basis: acoustic u-c, entropy, one shear wave per
- * tangential velocity, acoustic u+c.  Returns 0 if the Roe state is not
- * physical. */
-static int roe_eigensystem(const double *uL, const double *uR, int nc, double g,
-                           double Rm[OR_MAXC][OR_MAXC], double Lm[OR_MAXC][OR_MAXC])
+/* Roe average of two conserved states (normal-first ordering): density
+ * sqrt(rhoL rhoR), sqrt(rho)-weighted velocity and total enthalpy, and the
+ * sound speed c^2 = (gamma-1)(H - |u|^2/2).  roe[0] = rho, roe[1..nv] = u,
+ * roe[nv+1] = H, roe[nv+2] = c.  Returns 0 if c^2 <= 0 or a density <= 0. */
+static int roe_average(const double *uL, const double *uR, int nc, double g, double *roe)
 {
-    int nv = nc - 2;            /* number of velocity components */
+    int nv = nc - 2;
+    if (!(uL[0] > 0.0) || !(uR[0] > 0.0)) return 0;
     double sL = sqrt(uL[0]), sR = sqrt(uR[0]);
-    double vel[3], q2 = 0.0;
     double pL = pressure(uL, nc, g), pR = pressure(uR, nc, g);
     double HL = (uL[nc - 1] + pL) / uL[0], HR = (uR[nc - 1] + pR) / uR[0];
+    double q2 = 0.0;
+    roe[0] = sL * sR;
     for (int a = 0; a < nv; ++a) {
-        vel[a] = (sL * uL[1 + a] / uL[0] + sR * uR[1 + a] / uR[0]) / (sL + sR);
-        q2 += vel[a] * vel[a];
+        roe[1 + a] = (sL * uL[1 + a] / uL[0] + sR * uR[1 + a] / uR[0]) / (sL + sR);
+        q2 += roe[1 + a] * roe[1 + a];
     }
     double H = (sL * HL + sR * HR) / (sL + sR);
     double c2 = (g - 1.0) * (H - 0.5 * q2);
+    roe[nv + 1] = H;
     if (!(c2 > 0.0)) return 0;
-    double c = sqrt(c2), un = vel[0];
-    double b1 = (g - 1.0) / c2, b2 = 0.5 * q2 * b1;
+    roe[nv + 2] = sqrt(c2);
+    return 1;
+}
+
+/* Right (columns of Rm) and left (rows of Lm) eigenvectors of the
+ * primitive-variable Euler system V_t + A_V V_x = 0, V = (rho, u_n,
+ * u_t..., p) normal-first, at density rho and sound speed c (taken from the
+ * Roe average of the two cells sharing the face).  Waves in the order
+ * u-c, entropy, one shear wave per tangential velocity, u+c:
+ *   L rows: (0, -rho/(2c), 0, 1/(2c^2)), (1, 0, 0, -1/c^2), e_t, (0, rho/(2c), 0, 1/(2c^2))
+ *   R cols: (1, -c/rho, 0, c^2),         (1, 0, 0, 0),      e_t, (1, c/rho, 0, c^2). */
+static void prim_eigensystem(double rho, double c, int nc, double Rm[OR_MAXC][OR_MAXC], double Lm[OR_MAXC][OR_MAXC])
+{
+    int E = nc - 1;
     memset(Rm, 0, sizeof(double) * OR_MAXC * OR_MAXC);
     memset(Lm, 0, sizeof(double) * OR_MAXC * OR_MAXC);
-    int E = nc - 1;
-    /* wave 0: u - c */
-    Rm[0][0] = 1.0; Rm[1][0] = un - c;
-    for (int a = 1; a < nv; ++a) Rm[1 + a][0] = vel[a];
-    Rm[E][0] = H - un * c;
-    /* wave 1: entropy */
-    Rm[0][1] = 1.0; Rm[1][1] = un;
-    for (int a = 1; a < nv; ++a) Rm[1 + a][1] = vel[a];
-    Rm[E][1] = 0.5 * q2;
-    /* waves 2..nv: shear, one per tangential velocity */
-    for (int t = 1; t < nv; ++t) { Rm[1 + t][1 + t] = 1.0; Rm[E][1 + t] = vel[t]; }
-    /* wave nc-1: u + c */
-    Rm[0][E] = 1.0; Rm[1][E] = un + c;
-    for (int a = 1; a < nv; ++a) Rm[1 + a][E] = vel[a];
-    Rm[E][E] = H + un * c;
+    Lm[0][1] = -rho / (2.0 * c);
+    Lm[0][E] = 1.0 / (2.0 * c * c);
+    Lm[1][0] = 1.0;
+    Lm[1][E] = -1.0 / (c * c);
+    for (int t = 2; t < E; ++t) Lm[t][t] = 1.0;
+    Lm[E][1] = rho / (2.0 * c);
+    Lm[E][E] = 1.0 / (2.0 * c * c);
+    Rm[0][0] = 1.0;
+    Rm[1][0] = -c / rho;
+    Rm[E][0] = c * c;
+    Rm[0][1] = 1.0;
+    for (int t = 2; t < E; ++t) Rm[t][t] = 1.0;
+    Rm[0][E] = 1.0;
+    Rm[1][E] = c / rho;
+    Rm[E][E] = c * c;
+}
 
-    Lm[0][0] = 0.5 * (b2 + un / c);
-    Lm[0][1] = 0.5 * (-b1 * un - 1.0 / c);
-    for (int a = 1; a < nv; ++a) Lm[0][1 + a] = -0.5 * b1 * vel[a];
-    Lm[0][E] = 0.5 * b1;
-    Lm[1][0] = 1.0 - b2;
-    for (int a = 0; a < nv; ++a) Lm[1][1 + a] = b1 * vel[a];
-    Lm[1][E] = -b1;
-    for (int t = 1; t < nv; ++t) { Lm[1 + t][0] = -vel[t]; Lm[1 + t][1 + t] = 1.0; }
-    Lm[E][0] = 0.5 * (b2 - un / c);
-    Lm[E][1] = 0.5 * (-b1 * un + 1.0 / c);
-    for (int a = 1; a < nv; ++a) Lm[E][1 + a] = -0.5 * b1 * vel[a];
-    Lm[E][E] = 0.5 * b1;
-    return 1;
+/* Primitive variables (rho, u..., p) of a conserved state, same ordering. */
+static void to_primitive(const double *u, int nc, double g, double *v)
+{
+    v[0] = u[0];
+    for (int a = 1; a < nc - 1; ++a) v[a] = u[a] / u[0];
+    v[nc - 1] = pressure(u, nc, g);
+}
+
+static void to_conserved(const double *v, int nc, double g, double *u)
+{
+    double ke = 0.0;
+    u[0] = v[0];
+    for (int a = 1; a < nc - 1; ++a) {
+        u[a] = v[0] * v[a];
+        ke += v[a] * v[a];
+    }
+    u[nc - 1] = v[nc - 1] / (g - 1.0) + 0.5 * v[0] * ke;
 }
 
 /* GP-WENO prediction at one face centre from 2R+1 values f[0..2R] centred on
@@ -191,35 +211,43 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
     for (int a = 0; a < c->ndim; ++a) if (a != d) perm[k++] = 1 + a;
     perm[nc - 1] = nc - 1;
 
-    double st[OR_MAXS][OR_MAXC];           /* stencil, normal-first */
+    double st[OR_MAXS][OR_MAXC];           /* stencil, normal-first, conserved */
     for (int q = 0; q < ns; ++q) {
         int idx[3] = { cell[0], cell[1], cell[2] };
         idx[d] = map_index(c, d, s - R + q);
         long l = lin(c, idx[0], idx[1], idx[2]);
         for (int a = 0; a < nc; ++a) st[q][a] = U[(long)perm[a] * N + l];
     }
+    double roe[OR_MAXC + 1];
+    if (!roe_average(st[R], st[R + 1], nc, c->gamma, roe)) return 0;
     double Rm[OR_MAXC][OR_MAXC], Lm[OR_MAXC][OR_MAXC];
-    if (!roe_eigensystem(st[R], st[R + 1], nc, c->gamma, Rm, Lm)) return 0;
+    prim_eigensystem(roe[0], roe[nc], nc, Rm, Lm);
 
-    /* characteristic projection of every stencil cell */
+    /* characteristic projection of the primitive variables of every stencil cell */
     double ch[OR_MAXC][OR_MAXS];
-    for (int q = 0; q < ns; ++q)
+    for (int q = 0; q < ns; ++q) {
+        double v[OR_MAXC];
+        to_primitive(st[q], nc, c->gamma, v);
         for (int f = 0; f < nc; ++f) {
             double acc = 0.0;
-            for (int a = 0; a < nc; ++a) acc += Lm[f][a] * st[q][a];
+            for (int a = 0; a < nc; ++a) acc += Lm[f][a] * v[a];
             ch[f][q] = acc;
         }
+    }
     double wL[OR_MAXC], wR[OR_MAXC];
     for (int f = 0; f < nc; ++f) {
         wL[f] = gp_weno(c, &ch[f][0], c->wl, c->gl);   /* cells s-R..s+R, x* = +1/2 */
         wR[f] = gp_weno(c, &ch[f][1], c->wr, c->gr);   /* cells s+1-R..s+1+R, x* = -1/2 */
     }
-    double uL[OR_MAXC], uR[OR_MAXC];
+    double vL[OR_MAXC], vR[OR_MAXC], uL[OR_MAXC], uR[OR_MAXC];
     for (int a = 0; a < nc; ++a) {
         double l = 0.0, r = 0.0;
         for (int f = 0; f < nc; ++f) { l += Rm[a][f] * wL[f]; r += Rm[a][f] * wR[f]; }
-        uL[a] = l; uR[a] = r;
+        vL[a] = l; vR[a] = r;
     }
+    if (!(vL[0] > 0.0) || !(vR[0] > 0.0) || !(vL[nc - 1] > 0.0) || !(vR[nc - 1] > 0.0)) return 0;
+    to_conserved(vL, nc, c->gamma, uL);
+    to_conserved(vR, nc, c->gamma, uR);
     double pL = pressure(uL, nc, c->gamma), pR = pressure(uR, nc, c->gamma);
     if (!(uL[0] > 0.0) || !(uR[0] > 0.0) || !(pL > 0.0) || !(pR > 0.0)) return 0;
     double cL = sqrt(c->gamma * pL / uL[0]), cR = sqrt(c->gamma * pR / uR[0]);
@@ -351,15 +379,16 @@ int oracle_face(const oracle_cfg *c, int d, const double *st, double *uL, double
     return ok;
 }
 
-/* Eigen-system at the Roe average of two states (normal-first ordering),
- * exposed for unit tests. */
-int oracle_roe(int nc, double g, const double *uL, const double *uR, double *Rout, double *Lout)
+/* Roe average (rho, u..., H, c) of two conserved states and the primitive
+ * eigen-system at it (normal-first ordering), exposed for unit tests. */
+int oracle_roe(int nc, double g, const double *uL, const double *uR, double *roe, double *Rout, double *Lout)
 {
     double Rm[OR_MAXC][OR_MAXC], Lm[OR_MAXC][OR_MAXC];
-    int ok = roe_eigensystem(uL, uR, nc, g, Rm, Lm);
+    if (!roe_average(uL, uR, nc, g, roe)) return 0;
+    prim_eigensystem(roe[0], roe[nc], nc, Rm, Lm);
     for (int a = 0; a < nc; ++a)
         for (int b = 0; b < nc; ++b) { Rout[a * nc + b] = Rm[a][b]; Lout[a * nc + b] = Lm[a][b]; }
-    return ok;
+    return 1;
 }
 
 /* GP-WENO prediction exposed for unit tests: f has 2R+1 values. */

@@ -3,9 +3,10 @@
 // One call computes, for one face between stencil cells R and R+1 of a
 // (2R+2)-cell stencil along the face normal:
 //   - the Roe average of the two cells sharing the face and the left/right
-//     eigenvectors of the normal flux Jacobian there (characteristic
-//     variables, Section 6 of the paper);
-//   - the projection of every stencil cell on each characteristic field;
+//     eigenvectors of the primitive-variable system there (characteristic
+//     variables of V = (rho, u, p), Section 6 of the paper);
+//   - the projection of every stencil cell's primitive variables on each
+//     characteristic field;
 //   - per field, the GP-WENO left state (x* = x_i + dx/2 from the stencil of
 //     cell i) and right state (x* = x_{i+1} - dx/2 from the stencil of cell
 //     i+1): candidate predictions q^m = w_m . f_m (Eq. candidate_interp),
@@ -15,7 +16,7 @@
 //   - back-projection to conserved states U^L, U^R and the local
 //     Lax-Friedrichs flux F = (F(U^L)+F(U^R))/2 - alpha (U^R-U^L)/2 with
 //     alpha = max(|u_n|+c) over both states (Eq. riemann_prob).
-// Stencil values arrive "normal-first": (rho, m_normal, m_tangential..., E).
+// Stencil values arrive conserved and "normal-first": (rho, m_normal, m_tangential..., E).
 //
 // Nonlinear weights use the ratio form omega_m = gamma_m r_m^p / sum_s gamma_s r_s^p
 // with r_m = b_min / b_m, b_m = eps + beta_m.  It equals Eq. weights
@@ -105,65 +106,73 @@ __device__ __forceinline__ T weno_combine(const T (&q)[R + 1], const T (&b)[R + 
     return num * Num<T>::rcp(den);
 }
 
-// Reference state of the "cell-relative" flux evaluation (normal-first order).
+// Primitive reference state of the "cell-relative" evaluation (normal-first order).
 template <typename T, int NC>
-struct RefState {
-    T rho;            // density
-    T m[NC - 2];      // momentum components
-    T v[NC - 2];      // velocity components
-    T p;              // pressure
-    T hp;             // E + p
+struct PrimRef {
+    T rho;            // density of cell s
+    T u[NC - 2];      // velocity of cell s
+    T p;              // pressure of cell s
+    T hp;             // E + p of cell s
+    T mn;             // normal momentum rho u_n of cell s (the stored value)
 };
 
-// G(w) = F(U_ref + w) - F(U_ref): normal flux perturbation for a state
-// perturbation w, written so that every large quantity of the reference state
-// multiplies a small one (no cancellation of O(1) fluxes):
-//   dv_a = (w_m_a - v_a w_rho) / rho,        rho = rho_ref + w_rho
-//   p'   = (gamma-1) (w_E - 1/2 sum_a (m_a dv_a + v_a w_m_a))
-//   G    = (w_m_n,  m_n dv_n + v_n w_m_n + p',  m_t dv_n + v_n w_m_t,  v_n' (w_E + p') + dv_n (E+p)_ref)
-// with m = m_ref + w_m and v_n' = v_n + dv_n.  Returns false if rho <= 0 or
-// p <= 0 (or NaN) for the full state; `speed` = |u_n| + c of the full state.
+// For a primitive perturbation w = V - V_s (V = (rho, u_n, u_t..., p)):
+//   cw = U(V) - U(V_s)  (conservative perturbation)
+//   G  = F(V) - F(V_s)  (normal-flux perturbation)
+// written so that large reference quantities only multiply small ones:
+//   g_a = rho u_a - rho_s u_s,a = rho w_a + u_s,a w_rho,  rho = rho_s + w_rho,  u = u_s + w_u
+//   k   = rho|u|^2 - rho_s|u_s|^2 = sum_a (g_a u_a + rho_s u_s,a w_a)
+//   E'  = w_p/(gamma-1) + k/2
+//   G   = (g_n,  g_n u_n + m_s,n w_n + w_p,  g_n u_t + m_s,n w_t,  w_n (E+p)_s + u_n (E' + w_p)).
+// Returns false if rho <= 0 or p <= 0 (or NaN); speed = |u_n| + c of the full state.
 template <typename T, int NC>
-__device__ __forceinline__ bool pert_flux(const RefState<T, NC> &r, const T (&w)[NC], T gam, T (&G)[NC], T &speed)
+__device__ __forceinline__ bool prim_pert(const PrimRef<T, NC> &r, const T (&w)[NC], T gam, T igm1, T (&G)[NC],
+                                          T (&cw)[NC], T &speed)
 {
     constexpr int NV = NC - 2, E = NC - 1;
     const T rho = r.rho + w[0];
-    const T ir = Num<T>::rcp(rho);
-    T dv[NV], m[NV];
-    T k2 = T(0);
+    T u[NV], g[NV];
+    T k = T(0);
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-        dv[a] = fma(-r.v[a], w[0], w[1 + a]) * ir;
-        m[a] = r.m[a] + w[1 + a];
-        k2 = fma(m[a], dv[a], fma(r.v[a], w[1 + a], k2));
+        u[a] = r.u[a] + w[1 + a];
+        g[a] = fma(rho, w[1 + a], r.u[a] * w[0]);
+        k = fma(g[a], u[a], fma(r.rho * r.u[a], w[1 + a], k));
     }
-    const T pp = (gam - T(1)) * fma(T(-0.5), k2, w[E]);
-    const T vn = r.v[0] + dv[0];
-    G[0] = w[1];
-    G[1] = fma(m[0], dv[0], fma(r.v[0], w[1], pp));
+    const T ep = fma(w[E], igm1, T(0.5) * k);
+    cw[0] = w[0];
 #pragma unroll
-    for (int a = 1; a < NV; ++a) G[1 + a] = fma(m[a], dv[0], r.v[0] * w[1 + a]);
-    G[E] = fma(vn, w[E] + pp, dv[0] * r.hp);
-    const T pr = r.p + pp;
-    speed = Num<T>::fabs(vn) + Num<T>::sqrt(Num<T>::fmax(gam * pr * ir, T(1e-30)));
+    for (int a = 0; a < NV; ++a) cw[1 + a] = g[a];
+    cw[E] = ep;
+    G[0] = g[0];
+    G[1] = fma(g[0], u[0], fma(r.mn, w[1], w[E]));
+#pragma unroll
+    for (int a = 1; a < NV; ++a) G[1 + a] = fma(g[0], u[a], r.mn * w[1 + a]);
+    G[E] = fma(w[1], r.hp, u[0] * (ep + w[E]));
+    const T pr = r.p + w[E];
+    speed = Num<T>::fabs(u[0]) + Num<T>::sqrt(Num<T>::fmax(gam * pr * Num<T>::rcp(rho), T(1e-30)));
     return (rho > T(0)) && (pr > T(0));
 }
 
-// One face, cell-relative form.  st[0..2R+1] is the normal-first stencil; the
-// face s+1/2 lies between st[R] (cell s) and st[R+1] (cell s+1).  Outputs
+// One face, cell-relative form.  st[0..2R+1] is the normal-first conserved
+// stencil; the face s+1/2 lies between st[R] (cell s) and st[R+1] (cell s+1).
+// Outputs
 //   A = F_{s+1/2} - F(U_s)      (numerical face flux relative to cell s)
 //   B = F(U_{s+1}) - F(U_s)     (physical flux difference of the two cells)
 // so that the flux jump across cell s, F_{s+1/2} - F_{s-1/2} = A_s - A_{s-1} + B_{s-1},
 // is formed from small quantities only.  In real arithmetic this is exactly
-// the scheme (Roe-averaged characteristic projection, GP-WENO states by
-// Eqs. candidate_interp, beta-eigen, weights, weight_sum, Lax-Friedrichs
-// flux); the rewriting only changes where FP rounding falls:
-//   * characteristic data are projected as differences d_j = L (U_j - U_s)
-//     plus the centre value f_c = L U_s, so q^m = w_m . d_m + f_c sum_j w_mj and
-//     P_h . f_m = P_h . d_m + f_c sum_j P_hj (the sums are precomputed);
-//   * the left state is U_s + R (q_L - L U_s) and the right state
-//     U_{s+1} + R (q_R - L U_{s+1}), using R L = I and sum_m omega_m = 1;
-//   * fluxes are perturbations about U_s (pert_flux).
+// the scheme: characteristic variables of the primitive variables
+// V = (rho, u, p) with the eigenvectors of the primitive system at the Roe
+// average of cells s, s+1 (Section 6; "FD-Primitive"), GP-WENO states by
+// Eqs. candidate_interp, beta-eigen, weights, weight_sum, and the
+// Lax-Friedrichs flux.  The rewriting only changes where FP rounding falls:
+//   * primitive differences V_j - V_s come from the exact conserved
+//     differences U_j - U_s by perturbation algebra, and are projected as
+//     d_j = L (V_j - V_s) plus the centre value f_c = L V_s, so
+//     q^m = w_m . d_m + f_c sum_j w_mj and P_h . f_m = P_h . d_m + f_c sum_j P_hj;
+//   * the left state is V_s + R (q_L - L V_s) and the right state
+//     V_{s+1} + R (q_R - L V_{s+1}), using R L = I and sum_m omega_m = 1;
+//   * fluxes and conserved states are perturbations about V_s (prim_pert).
 // Returns false on a non-physical Roe, left, right or neighbour state.
 template <typename T, int NC, int R>
 __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
@@ -174,12 +183,13 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
     constexpr int NV = NC - 2;
     constexpr int S = R + 1, HALF = S / 2;
     const T gm1 = tb.gamma - T(1);
+    const T igm1 = Num<T>::rcp(gm1);
 
     // --- Roe average of the two cells sharing the face -------------------
     const T rL = st[R][0], rR = st[R + 1][0];
     const T rsL = Num<T>::rsqrt(rL), rsR = Num<T>::rsqrt(rR);
     const T inv = Num<T>::rcp(rL * rsL + rR * rsR);  // 1/(sqrt(rhoL)+sqrt(rhoR))
-    const T irL = rsL * rsL, irR = rsR * rsR;
+    const T irL = rsL * rsL;
     T vel[NV];
     T q2 = T(0), mL2 = T(0), mR2 = T(0);
 #pragma unroll
@@ -190,63 +200,73 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
         mR2 = fma(st[R + 1][1 + a], st[R + 1][1 + a], mR2);
     }
     const T pL = gm1 * fma(T(-0.5) * mL2, irL, st[R][E]);
-    const T pR = gm1 * fma(T(-0.5) * mR2, irR, st[R + 1][E]);
+    const T pR = gm1 * fma(T(-0.5) * mR2, rsR * rsR, st[R + 1][E]);
     const T H = fma(st[R][E] + pL, rsL, (st[R + 1][E] + pR) * rsR) * inv;
     const T c2 = gm1 * fma(T(-0.5), q2, H);
     bool ok = (rL > T(0)) && (rR > T(0)) && (c2 > T(0));
     const T ic = Num<T>::rsqrt(Num<T>::fmax(c2, T(1e-30)));
     const T c = c2 * ic;
-    const T un = vel[0];
-    const T b1 = gm1 * ic * ic;
-    const T b2 = T(0.5) * q2 * b1;
-    const T hb1 = T(0.5) * b1;
+    const T rbar = (rL * rsL) * (rR * rsR);   // sqrt(rhoL rhoR)
+    const T irb = rsL * rsR;                  // 1/rbar
+    // primitive eigenvectors at (rbar, c):
+    //   L rows: (0, -an, 0, ap), (1, 0, 0, -ie), e_t, (0, an, 0, ap)
+    //   R cols: (1, -c/rbar, 0, c^2), (1, 0, 0, 0), e_t, (1, c/rbar, 0, c^2)
+    const T an = T(0.5) * rbar * ic, ie = ic * ic, ap = T(0.5) * ie;
+    const T cr = c * irb;
 
-    // reference state: cell s
-    RefState<T, NC> ref;
+    // primitive reference: cell s
+    PrimRef<T, NC> ref;
     ref.rho = rL;
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-        ref.m[a] = st[R][1 + a];
-        ref.v[a] = st[R][1 + a] * irL;
-    }
+    for (int a = 0; a < NV; ++a) ref.u[a] = st[R][1 + a] * irL;
     ref.p = pL;
     ref.hp = st[R][E] + pL;
+    ref.mn = st[R][1];
+    T Vs[NC];
+    Vs[0] = rL;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) Vs[1 + a] = ref.u[a];
+    Vs[E] = pL;
 
-    // differences to cell s (D[R] is never used)
-    T D[NS][NC];
+    // primitive differences V_j - V_s from the exact conserved differences
+    T dV[NS][NC];
 #pragma unroll
-    for (int j = 0; j < NS; ++j)
+    for (int j = 0; j < NS; ++j) {
+        if (j == R) {
 #pragma unroll
-        for (int a = 0; a < NC; ++a) D[j][a] = (j == R) ? T(0) : st[j][a] - st[R][a];
-
-    // row k of L applied to a state
-    auto lrow = [&](int k, const T *u) -> T {
-        if (k == 0 || k == E) {
-            // acoustic rows: 1/2 (b2 +- un/c, -b1 un -+ 1/c, -b1 v_t, b1)
-            const T sgn = (k == 0) ? T(1) : T(-1);
-            T acc = fma(hb1, u[E], T(0.5) * fma(sgn * un, ic, b2) * u[0]);
-            acc = fma(T(-0.5) * fma(b1, un, sgn * ic), u[1], acc);
-#pragma unroll
-            for (int a = 1; a < NV; ++a) acc = fma(-hb1 * vel[a], u[1 + a], acc);
-            return acc;
-        } else if (k == 1) {
-            // entropy row: (1 - b2, b1 u_a..., -b1)
-            T acc = fma(-b1, u[E], (T(1) - b2) * u[0]);
-#pragma unroll
-            for (int a = 0; a < NV; ++a) acc = fma(b1 * vel[a], u[1 + a], acc);
-            return acc;
+            for (int a = 0; a < NC; ++a) dV[j][a] = T(0);
+            continue;
         }
-        // shear row of tangential velocity k-1: (-v_t, ..., 1, ...)
-        return fma(-vel[k - 1], u[0], u[k]);
+        T dU[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) dU[a] = st[j][a] - st[R][a];
+        const T irj = Num<T>::rcp(st[j][0]);
+        T k = T(0);
+        dV[j][0] = dU[0];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            const T du = fma(-ref.u[a], dU[0], dU[1 + a]) * irj;
+            dV[j][1 + a] = du;
+            k = fma(st[j][1 + a], du, fma(ref.u[a], dU[1 + a], k));
+        }
+        dV[j][E] = gm1 * fma(T(-0.5), k, dU[E]);
+    }
+
+    // row k of L_V applied to a primitive vector
+    auto lrow = [&](int kk, const T *v) -> T {
+        if (kk == 0) return fma(ap, v[E], -an * v[1]);
+        if (kk == E) return fma(ap, v[E], an * v[1]);
+        if (kk == 1) return fma(-ie, v[E], v[0]);
+        return v[kk];   // shear: tangential velocity
     };
 
     T dqL[NC], dqR[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-        const T fc = lrow(k, st[R]);
+    for (int kk = 0; kk < NC; ++kk) {
+        const T fc = lrow(kk, Vs);
         T d[NS];
 #pragma unroll
-        for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : lrow(k, D[j]);
+        for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : lrow(kk, dV[j]);
 
         // --- smoothness indicators on the R+2 windows d[w..w+R] --------
         T b[R + 2];
@@ -278,7 +298,7 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             b[w] = tb.eps + beta;
         }
         // --- candidates relative to the centre cells, both sides ---------
-        T cl[R + 1], cr[R + 1], bl[R + 1], br[R + 1];
+        T cl[R + 1], cr_[R + 1], bl[R + 1], br[R + 1];
 #pragma unroll
         for (int m = 0; m <= R; ++m) {
             T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
@@ -288,47 +308,39 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
                 if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
             }
             cl[m] = sl;
-            cr[m] = sr;
+            cr_[m] = sr;
             bl[m] = b[m];
             br[m] = b[m + 1];
         }
-        dqL[k] = weno_combine<T, R>(cl, bl, tb.gl, tb.p);              // q_L - L U_s
-        dqR[k] = weno_combine<T, R>(cr, br, tb.gr, tb.p) - d[R + 1];   // q_R - L U_{s+1}
+        dqL[kk] = weno_combine<T, R>(cl, bl, tb.gl, tb.p);              // q_L - L V_s
+        dqR[kk] = weno_combine<T, R>(cr_, br, tb.gr, tb.p) - d[R + 1];  // q_R - L V_{s+1}
     }
 
-    // --- back-projection: states relative to cell s -----------------------
-    T uL[NC], uR[NC];
-    {
-        const T hL = dqL[0] + dqL[1] + dqL[E], hR = dqR[0] + dqR[1] + dqR[E];
-        const T aL = c * (dqL[E] - dqL[0]), aR = c * (dqR[E] - dqR[0]);
-        uL[0] = hL;
-        uR[0] = D[R + 1][0] + hR;
-        uL[1] = fma(un, hL, aL);
-        uR[1] = D[R + 1][1] + fma(un, hR, aR);
-        T eL = fma(H, dqL[0] + dqL[E], fma(T(0.5) * q2, dqL[1], un * aL));
-        T eR = fma(H, dqR[0] + dqR[E], fma(T(0.5) * q2, dqR[1], un * aR));
+    // --- back-projection: primitive states relative to cell s -------------
+    T wL[NC], wR[NC];
+    wL[0] = dqL[0] + dqL[1] + dqL[E];
+    wR[0] = dV[R + 1][0] + (dqR[0] + dqR[1] + dqR[E]);
+    wL[1] = cr * (dqL[E] - dqL[0]);
+    wR[1] = fma(cr, dqR[E] - dqR[0], dV[R + 1][1]);
 #pragma unroll
-        for (int a = 1; a < NV; ++a) {
-            uL[1 + a] = fma(vel[a], hL, dqL[1 + a]);
-            uR[1 + a] = D[R + 1][1 + a] + fma(vel[a], hR, dqR[1 + a]);
-            eL = fma(vel[a], dqL[1 + a], eL);
-            eR = fma(vel[a], dqR[1 + a], eR);
-        }
-        uL[E] = eL;
-        uR[E] = D[R + 1][E] + eR;
+    for (int a = 2; a < E; ++a) {
+        wL[a] = dqL[a];
+        wR[a] = dV[R + 1][a] + dqR[a];
     }
+    wL[E] = c2 * (dqL[0] + dqL[E]);
+    wR[E] = fma(c2, dqR[0] + dqR[E], dV[R + 1][E]);
 
     // --- Lax-Friedrichs flux relative to F(U_s), and F(U_{s+1}) - F(U_s) ----
-    T GL[NC], GR[NC], sL, sR, sB;
-    ok = pert_flux<T, NC>(ref, uL, tb.gamma, GL, sL) && ok;
-    ok = pert_flux<T, NC>(ref, uR, tb.gamma, GR, sR) && ok;
+    T GL[NC], GR[NC], cL[NC], cR[NC], cB[NC], sL, sR, sB;
+    ok = prim_pert<T, NC>(ref, wL, tb.gamma, igm1, GL, cL, sL) && ok;
+    ok = prim_pert<T, NC>(ref, wR, tb.gamma, igm1, GR, cR, sR) && ok;
     T dn[NC];
 #pragma unroll
-    for (int a = 0; a < NC; ++a) dn[a] = D[R + 1][a];
-    ok = pert_flux<T, NC>(ref, dn, tb.gamma, B, sB) && ok;
+    for (int a = 0; a < NC; ++a) dn[a] = dV[R + 1][a];
+    ok = prim_pert<T, NC>(ref, dn, tb.gamma, igm1, B, cB, sB) && ok;
     const T alpha = Num<T>::fmax(sL, sR);
 #pragma unroll
-    for (int a = 0; a < NC; ++a) A[a] = T(0.5) * ((GL[a] + GR[a]) - alpha * (uR[a] - uL[a]));
+    for (int a = 0; a < NC; ++a) A[a] = T(0.5) * ((GL[a] + GR[a]) - alpha * (cR[a] - cL[a]));
     return ok;
 }
 

@@ -40,24 +40,59 @@ def rand_state(rng, nc, g=1.4):
     return np.concatenate([[rho], rho * vel, [p / (g - 1) + 0.5 * rho * (vel ** 2).sum()]])
 
 
+def conservative_jacobian(vel, H, g):
+    """Normal flux Jacobian dF/dU (normal-first) written in terms of velocity and total enthalpy
+    (textbook form; test-side)."""
+    nv = len(vel)
+    nc = nv + 2
+    u = vel[0]
+    q2 = sum(v * v for v in vel)
+    gm = g - 1.0
+    A = np.zeros((nc, nc))
+    A[0, 1] = 1.0
+    A[1, 0] = 0.5 * gm * q2 - u * u
+    A[1, 1] = (3.0 - g) * u
+    for t in range(1, nv):
+        A[1, 1 + t] = -gm * vel[t]
+        A[1 + t, 0] = -u * vel[t]
+        A[1 + t, 1] = vel[t]
+        A[1 + t, 1 + t] = u
+    A[1, nc - 1] = gm
+    A[nc - 1, 0] = u * (0.5 * gm * q2 - H)
+    A[nc - 1, 1] = H - gm * u * u
+    for t in range(1, nv):
+        A[nc - 1, 1 + t] = -gm * u * vel[t]
+    A[nc - 1, nc - 1] = g * u
+    return A
+
+
+def primitive_jacobian(rho, un, c, nc):
+    """A_V of V_t + A_V V_x = 0 for V = (rho, u_n, u_t..., p) (test-side, from the primitive
+    Euler equations: continuity, momentum with p_x/rho, advection, p_t + u p_x + rho c^2 u_x = 0)."""
+    A = np.eye(nc) * un
+    A[0, 1] = rho
+    A[1, nc - 1] = 1.0 / rho
+    A[nc - 1, 1] = rho * c * c
+    return A
+
+
 @pytest.mark.parametrize("nc", [3, 4, 5])
-def test_roe_eigensystem(nc):
+def test_roe_average_and_primitive_eigensystem(nc):
     rng = np.random.default_rng(nc)
     g = 1.4
     for _ in range(5):
         uL, uR = rand_state(rng, nc), rand_state(rng, nc)
-        Rm, Lm = oracle.roe_eigensystem(uL, uR, g)
-        np.testing.assert_allclose(Lm @ Rm, np.eye(nc), atol=1e-13)
-        # Roe average computed here from its definition (sqrt(rho) weights)
-        sL, sR = math.sqrt(uL[0]), math.sqrt(uR[0])
-        vel = [(sL * uL[a] / uL[0] + sR * uR[a] / uR[0]) / (sL + sR) for a in range(1, nc - 1)]
-        HL = (uL[-1] + (g - 1) * (uL[-1] - 0.5 * sum(uL[a] ** 2 for a in range(1, nc - 1)) / uL[0])) / uL[0]
-        HR = (uR[-1] + (g - 1) * (uR[-1] - 0.5 * sum(uR[a] ** 2 for a in range(1, nc - 1)) / uR[0])) / uR[0]
-        H = (sL * HL + sR * HR) / (sL + sR)
-        c = math.sqrt((g - 1) * (H - 0.5 * sum(v * v for v in vel)))
-        lam = np.array([vel[0] - c] + [vel[0]] * (nc - 2) + [vel[0] + c])
-        A = Rm @ np.diag(lam) @ Lm
+        roe, Rm, Lm = oracle.roe_eigensystem(uL, uR, g)
+        rho, vel, H, c = roe[0], roe[1:nc - 1], roe[nc - 1], roe[nc]
+        # Roe property of the averaged state: A(U_roe)(U_R - U_L) = F(U_R) - F(U_L)
+        A = conservative_jacobian(vel, H, g)
         np.testing.assert_allclose(A @ (uR - uL), euler_flux(uR, g) - euler_flux(uL, g), rtol=1e-12, atol=1e-12)
+        assert abs(rho - math.sqrt(uL[0] * uR[0])) < 1e-14
+        assert abs(c * c - (g - 1) * (H - 0.5 * (vel ** 2).sum())) < 1e-13
+        # primitive eigen-system at (rho, c)
+        np.testing.assert_allclose(Lm @ Rm, np.eye(nc), atol=1e-13)
+        lam = np.array([vel[0] - c] + [vel[0]] * (nc - 2) + [vel[0] + c])
+        np.testing.assert_allclose(Rm @ np.diag(lam) @ Lm, primitive_jacobian(rho, vel[0], c, nc), atol=1e-12)
 
 
 def test_correction_exact_for_degree5():
