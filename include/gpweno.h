@@ -169,18 +169,35 @@ gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *d
  * p <= 0 or a NaN; returns GPWENO_ERR_CUDA if an earlier launch failed. */
 gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 
-/* Batched 2D stepping: one persistent launch per RK stage serves n
- * independent 2D plans of possibly different grid size, R, l/dx and sigma
- * (all plans must share dtype and gamma).  The batch keeps references to the
- * plans' tables, which must outlive it.  tune_cache: path of a JSON file of
- * tuned schedule parameters, or NULL for the built-in cost model. */
+/* Batched 2D stepping (the task's batching pattern; same per-face scheme as
+ * gpweno_rk3_step): one persistent launch per RK stage serves n independent 2D
+ * plans of possibly different grid size, R, l/dx, sigma and boundary
+ * conditions (all plans must share dtype and device; at most 12 distinct
+ * (l/dx, sigma, gamma, eps, p) sets per radius).  The host cuts every
+ * instance into strips and row segments and hands each CTA a contiguous run of
+ * segments of equal estimated cost.  The batch refers to the member plans,
+ * which must outlive it.  tune_cache: NULL, or the path of a text file of
+ * lines "<signature hex> <block 128|256> <ctas per SM>" (written by
+ * paper_1808_04960_gb300/autotune.py); a line whose signature matches this
+ * batch overrides the built-in block-size choice.  Allocates its schedule and
+ * descriptor arrays on the device. */
 gpweno_status gpweno_plan_batch(gpweno_plan *out_batch, const gpweno_plan *plans, int n, const char *tune_cache);
 
-/* One SSP-RK3 step of every instance of a batch plan: U[k], scratch[k]
- * (2 state sizes) are device buffers of instance k; dt_dev: device array of
- * n doubles (instance time steps).  Three launches in total. */
+/* One SSP-RK3 step of every instance of a batch plan, in place:
+ * U[k] is instance k's state and scratch[k] its 4-state-size scratch (same
+ * layout and zero-initialised compensation as gpweno_rk3_step); dt_dev:
+ * device array of n doubles (per-instance time steps).  Three kernel
+ * launches in total; when the buffer pointers differ from the previous call,
+ * the first launch is preceded by one host-to-device copy of the instance
+ * descriptors (and a synchronisation of `stream`), so keep them fixed when
+ * capturing the step in a CUDA graph. */
 gpweno_status gpweno_batch_rk3_step(gpweno_plan batch, void *const *U, void *const *scratch, const void *dt_dev,
                                     void *stream);
+
+/* Schedule of a batch plan (for tuning and reports): block size, CTAs per SM
+ * assumed, CTAs per launch, number of segments, instance-list signature. */
+int gpweno_batch_info(gpweno_plan batch, int *block, int *ctas_per_sm, int *grid, int *segments,
+                      unsigned long long *signature);
 
 /* Number of kernel launches the last step function issued (for launch accounting). */
 int gpweno_last_launch_count(void);

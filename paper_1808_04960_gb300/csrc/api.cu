@@ -172,7 +172,10 @@ gpweno_status gpweno_plan_destroy(gpweno_plan p)
 {
     if (!p) return GPWENO_OK;
     if (p->ws) cudaFree(p->ws);
-    if (p->batch_dev) cudaFree(p->batch_dev);
+    if (p->batch_inst_dev) cudaFree(p->batch_inst_dev);
+    if (p->batch_inst_host) cudaFreeHost(p->batch_inst_host);
+    if (p->batch_segs_dev) cudaFree(p->batch_segs_dev);
+    if (p->batch_cta_dev) cudaFree(p->batch_cta_dev);
     delete p;
     return GPWENO_OK;
 }
@@ -341,24 +344,83 @@ gpweno_status gpweno_flags(gpweno_plan p, int *nonphysical)
 
 gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int n, const char *tune_cache)
 {
-    (void)tune_cache;
-    if (out) *out = nullptr;
-    set_error("gpweno_plan_batch: not available in this build");
-    (void)plans;
-    (void)n;
-    return GPWENO_ERR_ARG;
+    if (!out || !plans || n < 1) {
+        set_error("gpweno_plan_batch: need an output pointer and at least one plan");
+        return GPWENO_ERR_ARG;
+    }
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        gpweno_plan p = plans[k];
+        if (!p || p->is_batch || p->dims.ndim != 2) {
+            set_error("gpweno_plan_batch: plan %d is not a 2D single-grid plan", k);
+            return GPWENO_ERR_ARG;
+        }
+        if (p->opts.dtype != plans[0]->opts.dtype || p->device != plans[0]->device) {
+            set_error("gpweno_plan_batch: plan %d differs in dtype or device from plan 0", k);
+            return GPWENO_ERR_ARG;
+        }
+    }
+    gpweno_plan b = new (std::nothrow) gpweno_plan_s();
+    if (!b) {
+        set_error("out of host memory");
+        return GPWENO_ERR_ARG;
+    }
+    b->is_batch = true;
+    b->members.assign(plans, plans + n);
+    b->opts = plans[0]->opts;
+    b->device = plans[0]->device;
+    b->num_sms = plans[0]->num_sms;
+    b->dims.ndim = 2;
+    if (tune_cache) b->batch_tune_path = tune_cache;
+    cudaError_t e = cudaMalloc(&b->ws, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->ws, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        gpweno_plan_destroy(b);
+        return cuda_fail(e, "gpweno_plan_batch workspace");
+    }
+    gpweno_status s = b->opts.dtype == GPWENO_F32 ? build_batch_f32(b) : build_batch_f64(b);
+    if (s != GPWENO_OK) {
+        gpweno_plan_destroy(b);
+        return s;
+    }
+    *out = b;
+    return GPWENO_OK;
 }
 
-gpweno_status gpweno_batch_rk3_step(gpweno_plan batch, void *const *U, void *const *scratch, const void *dt_dev,
+gpweno_status gpweno_batch_rk3_step(gpweno_plan b, void *const *U, void *const *scratch, const void *dt_dev,
                                     void *stream)
 {
-    (void)batch;
-    (void)U;
-    (void)scratch;
-    (void)dt_dev;
-    (void)stream;
-    set_error("gpweno_batch_rk3_step: not available in this build");
-    return GPWENO_ERR_ARG;
+    g_launches = 0;
+    if (!b || !b->is_batch || !U || !scratch || !dt_dev) {
+        set_error("gpweno_batch_rk3_step: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    const int n = (int)b->members.size();
+    for (int k = 0; k < n; ++k)
+        if (!U[k] || !scratch[k] || !aligned16(U[k]) || !aligned16(scratch[k])) {
+            set_error("gpweno_batch_rk3_step: buffers of instance %d missing or not 16-byte aligned", k);
+            return GPWENO_ERR_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *dt = static_cast<const double *>(dt_dev);
+    for (int stage = 0; stage < 3; ++stage) {
+        gpweno_status s = b->opts.dtype == GPWENO_F32 ? launch_batch_stage_f32(b, stage, U, scratch, dt, st)
+                                                      : launch_batch_stage_f64(b, stage, U, scratch, dt, st);
+        if (s != GPWENO_OK) return s;
+    }
+    return GPWENO_OK;
+}
+
+int gpweno_batch_info(gpweno_plan b, int *block, int *ctas_per_sm, int *grid, int *segments,
+                      unsigned long long *signature)
+{
+    if (!b || !b->is_batch) return GPWENO_ERR_ARG;
+    if (block) *block = b->batch_nt;
+    if (ctas_per_sm) *ctas_per_sm = b->batch_ctas_per_sm;
+    if (grid) *grid = b->batch_grid;
+    if (segments) *segments = b->batch_nseg;
+    if (signature) *signature = b->batch_signature;
+    return GPWENO_OK;
 }
 
 }  // extern "C"

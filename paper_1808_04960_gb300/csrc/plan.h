@@ -32,11 +32,19 @@ struct gpweno_plan_s {
     bool is_batch = false;
     // batch-only data
     std::vector<gpweno_plan> members;
-    void *batch_dev = nullptr;     // device copy of per-instance descriptors
-    size_t batch_bytes = 0;
-    int batch_items = 0;
-    int batch_grid = 0;
-    std::vector<long> member_ncell;
+    int batch_nt = 256;                     // block size of the batch kernel
+    int batch_ctas_per_sm = 2;              // resident CTAs per SM the schedule assumes
+    int batch_grid = 0;                     // CTAs per launch
+    int batch_nseg = 0;                     // segments in the schedule
+    unsigned long long batch_signature = 0; // hash of the instance list (tuning-cache key)
+    std::string batch_tune_path;            // tuning cache file (may be empty)
+    std::vector<unsigned char> batch_tables;   // BatchTables<T> bytes (kernel parameter)
+    std::vector<int> member_tab;            // table set index per instance
+    void *batch_inst_dev = nullptr;         // BatchInst<T>[n]
+    void *batch_inst_host = nullptr;        // pinned staging of the same
+    void *batch_segs_dev = nullptr;         // BatchSeg[nseg]
+    void *batch_cta_dev = nullptr;          // int[grid+1]
+    std::vector<const void *> batch_last_ptrs;  // U/scratch pointers of the last upload
 };
 
 namespace gpweno {

@@ -68,6 +68,8 @@ def load(path: str | None = None):
             "gpweno_plan_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, ctypes.c_char_p]),
             "gpweno_batch_rk3_step": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]),
             "gpweno_last_launch_count": (i, []),
+            "gpweno_batch_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_ulonglong)]),
             "gpweno_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sigs.items():
@@ -276,6 +278,20 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+    def info(self) -> dict:
+        """Schedule of the batch: block size, CTAs per SM, CTAs per launch, segments, signature."""
+        v = [ctypes.c_int() for _ in range(4)]
+        sig = ctypes.c_ulonglong()
+        _check(self.lib.gpweno_batch_info(self.handle, *[ctypes.byref(x) for x in v], ctypes.byref(sig)),
+               "gpweno_batch_info")
+        return dict(block=v[0].value, ctas_per_sm=v[1].value, grid=v[2].value, segments=v[3].value,
+                    signature=f"{sig.value:016x}")
+
+    def flags(self) -> int:
+        v = ctypes.c_int(0)
+        _check(self.lib.gpweno_flags(self.handle, ctypes.byref(v)), "gpweno_flags")
+        return int(v.value)
 
     def rk3_step(self, Us, scratches, dt_dev, stream=None):
         import torch
