@@ -238,6 +238,8 @@ def run_gpu(args):
     e2e = {"value": ws * cells * 3 * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
            "d2h_bytes_per_step": nb, "ms_per_step": e2e_ms / args.steps}
 
+    batch = run_batch(args, stream) if args.batch_count > 0 else None
+
     if rank != 0:
         return None
     peaks, peak_kind = read_peaks()
@@ -269,12 +271,69 @@ def run_gpu(args):
                          "frac": hbm_ach / peaks.get("hbm_gbs"), "peak_kind": peak_kind,
                          "bytes_per_cell_stage": hbm_bytes_per_cell_stage(4)},
         "e2e": e2e,
+        "batch": batch,
         "gpu_launches": r32["launches_per_step"] * args.steps,
         "clocks": r32["clocks"],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, dt)
     return line
+
+
+def run_batch(args, stream):
+    """Batched workload: `--batch-count` seeded 2D instances (n_x, n_y log-uniform on [64, 1024],
+    R in {1,2,3}, l/dx in {6,12,24}, half four-quadrant, half vortex), FP32, per-instance CFL dt.
+    One persistent launch per RK stage (CUDA graph of the step) against per-instance launches."""
+    import torch
+
+    from paper_1808_04960_gb300 import gpweno, workloads
+    insts = workloads.batch_instances(args.batch_count, seed=5)
+    plans, Us, Ss, dts = [], [], [], []
+    for inst in insts:
+        m = inst["meta"]
+        p = gpweno.Plan(inst["R"], inst["ell_over_dx"], inst["U"].shape[1:], m["dx"], m["bc"], dtype="f32")
+        U = torch.from_numpy(inst["U"]).to("cuda", torch.float32).contiguous()
+        d = torch.zeros(1, dtype=torch.float64, device="cuda")
+        p.cfl_dt(U, 0.4, d)
+        plans.append(p)
+        Us.append(U)
+        Ss.append(p.new_scratch())
+        dts.append(d)
+    dt_dev = torch.cat(dts)
+    dt_host = dt_dev.cpu().tolist()
+    cells = sum(i["nx"] * i["ny"] for i in insts)
+    cache = os.path.join(ROOT, "paper_1808_04960_gb300", "tune_cache.txt")
+    batch = gpweno.BatchPlan(plans, tune_cache=cache)
+    for _ in range(2):
+        batch.rk3_step(Us, Ss, dt_dev, stream=stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.rk3_step(Us, Ss, dt_dev)
+    g.replay()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    for _ in range(args.batch_steps):
+        g.replay()
+    e[1].record(stream)
+    # per-instance launches (3 per instance per step), no graph
+    e[2].record(stream)
+    for _ in range(args.batch_steps):
+        for p, U, S, dt in zip(plans, Us, Ss, dt_host):
+            p.rk3_step(U, S, dt=dt, stream=stream)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    ms_b = e[0].elapsed_time(e[1]) / args.batch_steps
+    ms_u = e[2].elapsed_time(e[3]) / args.batch_steps
+    nonphys = batch.flags()
+    info = batch.info()
+    return {"workload": f"{len(insts)} seeded 2D instances, n_x,n_y log-uniform on [64,1024], R in {{1,2,3}}, "
+                        "l/dx in {6,12,24}, four-quadrant/vortex, FP32, per-instance CFL 0.4",
+            "instances": len(insts), "cells": cells, "steps": args.batch_steps,
+            "value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+            "unbatched_value": cells * 3 / (ms_u * 1e-3), "unbatched_ms_per_step": ms_u,
+            "speedup_vs_unbatched": ms_u / ms_b, "launches_per_step": 3,
+            "unbatched_launches_per_step": 3 * len(insts), "schedule": info, "nonphysical_flag": nonphys}
 
 
 def cpu_baseline(args, dt_full, gpu_compare=True):
@@ -364,6 +423,8 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtypes", default="f32,f64", help="comma list; f32 is always first and required")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -44,12 +44,6 @@ struct BatchSeg {
     int inst, strip, y0, y1;
 };
 
-template <typename T>
-constexpr int batch_occupancy_hint()
-{
-    return sizeof(T) == 4 ? 2 : 1;
-}
-
 template <typename T, int NT>
 constexpr size_t batch_smem_bytes()
 {
@@ -57,8 +51,9 @@ constexpr size_t batch_smem_bytes()
     return stage2d_smem_bytes<T, 3, NT>();
 }
 
+// 512 (FP32) or 256 (FP64) resident threads per SM at most 128 / 255 registers each
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT)
     batch_stage_kernel(const BatchInst<T> *__restrict__ inst, const BatchSeg *__restrict__ segs,
                        const int *__restrict__ cta_start, int stage, const double *__restrict__ dt_dev, int *flags,
                        const __grid_constant__ BatchTables<T> bt)
