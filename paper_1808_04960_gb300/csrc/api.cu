@@ -83,10 +83,6 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
         set_error("ndim=%d must be 1, 2 or 3", dims->ndim);
         return GPWENO_ERR_ARG;
     }
-    if (dims->ndim == 3) {
-        set_error("ndim=3 is not supported by this build");
-        return GPWENO_ERR_ARG;
-    }
     if (!(gamma_gas > 1.0)) {
         set_error("gamma=%g must exceed 1", gamma_gas);
         return GPWENO_ERR_ARG;
@@ -230,7 +226,9 @@ gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, 
     StageIO io;
     io.dt = dt;
     io.dt_dev = dt_dev;
-    // D_1 = dt L(U^n), V_1 = U^n + D_1
+    // D_1 = dt L(U^n), V_1 = U^n + D_1   (3D: the x+y part of L goes through the
+    // buffer the stage update overwrites next: V1, V2, then the dead V1)
+    io.P = V1;
     io.U = U;
     io.U0 = U;
     io.Dout = D;
@@ -242,12 +240,14 @@ gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, 
     io.U = V1;
     io.Din = D;
     io.Vout = V2;
+    io.P = V2;
     io.b = 0.25;
     if ((s = launch_stage(p, io, st)) != GPWENO_OK) return s;
     // U^{n+1} = U^n + 2/3 (D_2 + dt L(V_2)), compensated with lo
     io.U = V2;
     io.Dout = nullptr;
     io.Vout = nullptr;
+    io.P = V1;
     io.out = U;
     io.lo = lo;
     io.b = 2.0 / 3.0;
@@ -276,6 +276,7 @@ gpweno_status gpweno_rhs(gpweno_plan p, const void *U, void *dUdt, void *stream)
     StageIO io;
     io.U = U;
     io.out = dUdt;
+    io.P = dUdt;
     io.mode = 0;
     return launch_stage(p, io, (cudaStream_t)stream);
 }

@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT)
                 a.mode = kModeFinal;
                 a.u0_is_stencil = 0;
             }
+            a.cstride = (long)I.n[0] * I.n[1];
+            a.P = nullptr;
             sa = a;
             ssg = sg;
             sR = I.R;

@@ -63,6 +63,8 @@ StageArgs<T> base_args(const gpweno_plan_s *p)
         a.idx[d] = (T)(1.0 / p->dims.dx[d]);
     }
     a.flags = reinterpret_cast<int *>(p->ws + 3);
+    a.cstride = p->ncell;
+    a.P = nullptr;
     return a;
 }
 
@@ -71,7 +73,51 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
 {
     StageArgs<T> a = a0;
     const FaceTables<T, R> tb = make_tables<T, R>(p);
-    if (p->dims.ndim == 2) {
+    if (p->dims.ndim == 3) {
+        constexpr int NT = kNT2D;
+        // (1) xy-plane kernel: P = -(div_x/dx + div_y/dy)
+        {
+            const size_t smem = stage2d_smem_bytes<T, R, NT, 5>();
+            auto kern = plane3d_kernel<T, R, NT>;
+            static int occ = 0;
+            if (!occ) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return cuda_fail(e, "plane3d smem attribute");
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+                if (e != cudaSuccess || occ < 1)
+                    return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "plane3d occupancy");
+            }
+            StageArgs<T> pa = a;
+            const int wmax = NT - 5;
+            pa.nstrips = (a.n[0] + wmax - 1) / wmax;
+            pa.W = (a.n[0] + pa.nstrips - 1) / pa.nstrips;
+            pa.mode = kModePartial;
+            pa.out = const_cast<T *>(a.P);
+            pa.rate = nullptr;
+            const long long rows = (long long)pa.nstrips * a.n[1] * a.n[2];
+            const int grid = (int)std::max(1LL, std::min<long long>((long long)occ * p->num_sms, rows / 8));
+            kern<<<grid, NT, smem, st>>>(pa, tb);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "plane3d kernel launch");
+            count_launch(1);
+        }
+        // (2) z-marching kernel: L = P - div_z/dz and the stage update
+        {
+            const size_t smem = stagez_smem_bytes<T, R, NT>();
+            auto kern = stagez_kernel<T, R, NT>;
+            static int occ = 0;
+            if (!occ) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return cuda_fail(e, "stagez smem attribute");
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+                if (e != cudaSuccess || occ < 1)
+                    return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "stagez occupancy");
+            }
+            const long long cols = ((long long)a.n[0] * a.n[1] + NT - 1) / NT * a.n[2];
+            const int grid = (int)std::max(1LL, std::min<long long>((long long)occ * p->num_sms, cols / 8));
+            kern<<<grid, NT, smem, st>>>(a, tb);
+        }
+    } else if (p->dims.ndim == 2) {
         constexpr int NT = kNT2D;
         const size_t smem = stage2d_smem_bytes<T, R, NT>();
         auto kern = stage2d_kernel<T, R, NT>;
@@ -116,6 +162,7 @@ gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
     a.Dout = static_cast<T *>(io.Dout);
     a.Vout = static_cast<T *>(io.Vout);
     a.out = static_cast<T *>(io.out);
+    a.P = static_cast<const T *>(io.P);
     a.lo = static_cast<T *>(io.lo);
     a.u0_is_stencil = io.U0 == io.U ? 1 : 0;
     a.b = (T)io.b;
@@ -137,7 +184,9 @@ gpweno_status launch_max_rate_T(gpweno_plan p, const void *U, cudaStream_t st)
     StageArgs<T> a = base_args<T>(p);
     a.rate = p->ws;
     const int blocks = (int)std::min<long>((p->ncell + 255) / 256, 4L * p->num_sms);
-    if (p->dims.ndim == 2)
+    if (p->dims.ndim == 3)
+        max_rate_kernel<T, 5><<<blocks, 256, 0, st>>>(static_cast<const T *>(U), p->ncell, a, (T)p->gamma);
+    else if (p->dims.ndim == 2)
         max_rate_kernel<T, 4><<<blocks, 256, 0, st>>>(static_cast<const T *>(U), p->ncell, a, (T)p->gamma);
     else
         max_rate_kernel<T, 3><<<blocks, 256, 0, st>>>(static_cast<const T *>(U), p->ncell, a, (T)p->gamma);

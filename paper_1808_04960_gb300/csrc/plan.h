@@ -62,6 +62,7 @@ struct StageIO {
     void *Vout = nullptr;        // U^n + increment (mode 1)
     void *out = nullptr;         // RHS (mode 0) or U^{n+1} (mode 2)
     void *lo = nullptr;          // compensation remainder (mode 2)
+    void *P = nullptr;           // 3D: buffer for the x+y part of L (read back cell by cell)
     double b = 1.0;
     int mode = 0;
     double dt = 0.0;

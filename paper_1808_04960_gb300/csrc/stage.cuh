@@ -33,7 +33,9 @@ namespace gpweno {
 // stored with their own relative precision, and the final sum is compensated
 // (TwoSum) with a running remainder `lo`, so state rounding does not
 // accumulate over many steps.
-enum StageMode { kModeRHS = 0, kModeIncrement = 1, kModeFinal = 2 };
+enum StageMode { kModeRHS = 0, kModeIncrement = 1, kModeFinal = 2, kModePartial = 3 };
+// kModePartial (3D only): the xy-plane kernel writes its part of L, -(div_x/dx + div_y/dy),
+// to `out`; the z-marching kernel adds the z part and applies modes 0-2.
 
 template <typename T>
 struct StageArgs {
@@ -50,6 +52,8 @@ struct StageArgs {
     T b;                       // stage weight b_k
     int mode;                  // StageMode
     int u0_is_stencil;         // U0 == U: take U^n from the staged stencil data
+    long cstride;              // distance between components (cells of the whole grid)
+    const T *P;                // z kernel: x+y part of L written by the plane kernel
     const double *dt_dev;      // device dt (or null: use dt)
     double dt;
     unsigned long long *rate;  // if non-null: atomic max of (|u_d| + c)/dx_d of the result (double bits)
@@ -84,11 +88,11 @@ struct Ring2D {
     static __device__ __forceinline__ int slot(int g) { return g & (ROWS - 1); }
 };
 
-template <typename T, int R, int NT>
+template <typename T, int R, int NT, int NC = 4>
 constexpr size_t stage2d_smem_bytes()
 {
     using RG = Ring2D<R, NT>;
-    return sizeof(T) * (size_t)(RG::ROWS * 4 * RG::STRIDE + 2 * 4 * NT);
+    return sizeof(T) * (size_t)(RG::ROWS * NC * RG::STRIDE + 2 * NC * NT);
 }
 
 // Error-free sum a + b = s + e (Knuth's TwoSum).
@@ -142,21 +146,21 @@ __device__ __forceinline__ void rates2d(const T (&u)[4], T gam, const T (&idx)[3
     ry = (Num<T>::fabs(vy) + c) * idx[1];
 }
 
-// One segment: rows [y0, y1) of strip `strip`.
-template <typename T, int R, int NT>
+// One segment: rows [y0, y1) of strip `strip` of the xy-plane starting at cell offset zoff.
+// NC = 4 (2D) or 5 (an xy-plane of a 3D grid).
+template <typename T, int R, int NT, int NC = 4>
 __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, int strip, int y0,
-                                                int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok)
+                                                int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok, long zoff = 0)
 {
     using RG = Ring2D<R, NT>;
     constexpr int G = RG::G, ROWS = RG::ROWS, STRIDE = RG::STRIDE;
-    constexpr int NC = 4;
     constexpr int NS = 2 * R + 2;
     T *ring = smem;                              // [ROWS][NC][STRIDE]
     T *FA = smem + ROWS * NC * STRIDE;           // [NC][NT]  x-face A = F_{s+1/2} - F(U_s)
     T *FB = FA + NC * NT;                        // [NC][NT]  x-face B = F(U_{s+1}) - F(U_s)
     const int tid = threadIdx.x;
     const int nx = a.n[0], ny = a.n[1];
-    const long plane = (long)nx * ny;
+    const long plane = a.cstride;
     const int x0 = strip * a.W;
     const int Wc = min(a.W, nx - x0);
     const int s_begin = y0 - 3, s_end = y1 + 1;
@@ -166,7 +170,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     auto load_row = [&](int g) {
         const int gy = bc_map(g, ny, a.per[1]);
         T *dst = ring + RG::slot(g) * (NC * STRIDE);
-        const T *src = a.U + (long)gy * nx;
+        const T *src = a.U + zoff + (long)gy * nx;
         for (int col = tid; col < rowlen; col += NT) {
             const int gx = bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
@@ -200,8 +204,8 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         // U^n, previous increment and remainder of this thread's output cell,
         // in flight during the face work
         T u0[NC], din[NC], lov[NC];
-        const long cell = (long)r * nx + x0 + tid;
-        const bool epi = out_row && col_ok && a.mode != kModeRHS;
+        const long cell = zoff + (long)r * nx + x0 + tid;
+        const bool epi = out_row && col_ok && (a.mode == kModeIncrement || a.mode == kModeFinal);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             u0[c] = (epi && !a.u0_is_stencil) ? a.U0[c * plane + cell] : T(0);
@@ -215,15 +219,19 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 const T *row = ring + RG::slot(s - R + q) * (NC * STRIDE) + G + tid;
-                st[q][0] = row[0];
-                st[q][1] = row[2 * STRIDE];   // normal momentum: rho v
-                st[q][2] = row[1 * STRIDE];   // tangential: rho u
-                st[q][3] = row[3 * STRIDE];
+                // normal-first for a y-face: (rho, rho v, rho u, [rho w], E)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) st[q][c] = row[(c == 1 ? 2 : (c == 2 ? 1 : c)) * STRIDE];
             }
             T An[NC], Bn[NC];
             ok = face_rel<T, NC, R>(st, tb, An, Bn) && ok;
-            const T Ac[NC] = {An[0], An[2], An[1], An[3]};   // back to (rho, rho u, rho v, E)
-            const T Bc[NC] = {Bn[0], Bn[2], Bn[1], Bn[3]};
+            T Ac[NC], Bc[NC];   // back to natural order
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int pc = c == 1 ? 2 : (c == 2 ? 1 : c);
+                Ac[c] = An[pc];
+                Bc[c] = Bn[pc];
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -267,12 +275,17 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 const T divx = corrected_divergence<T>(dx[0], dx[1], dx[2], dx[3], dx[4]);
                 const T divy = corrected_divergence<T>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
                 const T L = -fma(divx, idx[0], divy * idx[1]);
-                const T un = a.u0_is_stencil ? urow[c * STRIDE] : u0[c];
-                res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt);
+                if (NC == 5 || a.mode == kModePartial) {
+                    a.out[c * plane + cell] = L;
+                    res[c] = L;
+                } else {
+                    const T un = a.u0_is_stencil ? urow[c * STRIDE] : u0[c];
+                    res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt);
+                }
             }
-            if (a.rate && a.mode == kModeFinal) {
+            if (NC == 4 && a.rate && a.mode == kModeFinal) {
                 T rx, ry;
-                rates2d<T>(res, tb.gamma, idx, rx, ry);
+                rates2d<T>(reinterpret_cast<const T(&)[4]>(res), tb.gamma, idx, rx, ry);
                 rmx = Num<T>::fmax(rmx, rx);
                 rmy = Num<T>::fmax(rmy, ry);
             }
@@ -326,6 +339,190 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
         u += y1 - y0;
     }
     finish_block<T>(a, rmx, rmy, T(0), ok);
+}
+
+// ---------------------------------------------------------------------------
+// 3D.  Each stage is two launches: the xy-plane kernel below runs the 2D
+// column-strip marching routine (5 components) on every z-plane and writes
+// -(div_x/dx + div_y/dy) to a stage buffer P; the z-marching kernel then walks
+// contiguous runs of xy-columns along z, evaluates each z-face once, adds
+// -div_z/dz to P and applies the stage update.  P is a buffer the update later
+// overwrites cell by cell (each cell reads its own P first), so 3D needs no
+// scratch beyond 2D's.
+template <typename T, int R, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    T rmx = T(0), rmy = T(0);
+    bool ok = true;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const long per_plane = (long)a.nstrips * ny;
+    const long total = per_plane * nz;
+    long long u = (long long)total * blockIdx.x / gridDim.x;
+    const long long uend = (long long)total * (blockIdx.x + 1) / gridDim.x;
+    while (u < uend) {
+        const int z = (int)(u / per_plane);
+        const long rem = u - (long long)z * per_plane;
+        const int strip = (int)(rem / ny);
+        const int y0 = (int)(rem - (long)strip * ny);
+        const int y1 = (int)min((long long)ny, y0 + (uend - u));
+        stage2d_segment<T, R, NT, 5>(a, tb, strip, y0, y1, smem, T(0), rmx, rmy, ok, (long)z * nx * ny);
+        u += y1 - y0;
+    }
+    if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.flags, 1);
+}
+
+template <int R>
+struct RingZ {
+    static constexpr int LOW = R > 2 ? R : 2;
+    static constexpr int NEEDED = LOW + R + 3;
+    static constexpr int ROWS = NEEDED <= 8 ? 8 : 16;
+    static __device__ __forceinline__ int slot(int g) { return g & (ROWS - 1); }
+};
+
+template <typename T, int R, int NT>
+constexpr size_t stagez_smem_bytes()
+{
+    return sizeof(T) * (size_t)(RingZ<R>::ROWS * 5 * NT);
+}
+
+template <typename T>
+__device__ __forceinline__ void rates3d(const T (&u)[5], T gam, const T (&idx)[3], T &rx, T &ry, T &rz)
+{
+    const T ir = Num<T>::rcp(u[0]);
+    const T vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
+    const T pr = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * vx + u[2] * vy + u[3] * vz));
+    const T c = Num<T>::sqrt(Num<T>::fmax(gam * pr * ir, T(0)));
+    rx = (Num<T>::fabs(vx) + c) * idx[0];
+    ry = (Num<T>::fabs(vy) + c) * idx[1];
+    rz = (Num<T>::fabs(vz) + c) * idx[2];
+}
+
+// z-marching over columns [c0, c0+NT) of the flattened xy-plane, planes [z0, z1).
+template <typename T, int R, int NT>
+__device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, long c0, int z0,
+                                               int z1, T *ring, T dt, T (&rm)[3], bool &ok)
+{
+    using RZ = RingZ<R>;
+    constexpr int NC = 5, NS = 2 * R + 2;
+    const int tid = threadIdx.x;
+    const int nz = a.n[2];
+    const long plane = (long)a.n[0] * a.n[1];
+    const long cs = a.cstride;
+    const long col = c0 + tid;
+    const bool col_ok = col < plane;
+    const int s_begin = z0 - 3, s_end = z1 + 1;
+    const T idx[3] = {a.idx[0], a.idx[1], a.idx[2]};
+
+    auto load_plane = [&](int g) {
+        if (!col_ok) return;
+        const int gz = bc_map(g, nz, a.per[2]);
+        T *dst = ring + RZ::slot(g) * (NC * NT) + tid;
+        const T *src = a.U + (long)gz * plane + col;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * NT, src + c * cs);
+    };
+    for (int g = s_begin - R; g <= s_begin + 1 + R; ++g) load_plane(g);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    T Dz[5][NC], Ap[NC], Bp[NC];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Dz[k][c] = T(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Ap[c] = Bp[c] = T(0);
+
+    for (int s = s_begin; s <= s_end; ++s) {
+        if (s < s_end) load_plane(s + 2 + R);
+        cp_async_commit();
+        const int r = s - 2;
+        const bool out = r >= z0 && col_ok;
+        const long cell = (long)r * plane + col;
+        T pv[NC], u0[NC], din[NC], lov[NC];
+        const bool epi = out && (a.mode == kModeIncrement || a.mode == kModeFinal);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            pv[c] = out ? a.P[c * cs + cell] : T(0);
+            u0[c] = (epi && !a.u0_is_stencil) ? a.U0[c * cs + cell] : T(0);
+            din[c] = (epi && a.Din) ? a.Din[c * cs + cell] : T(0);
+            lov[c] = (epi && a.lo && a.mode == kModeFinal) ? a.lo[c * cs + cell] : T(0);
+        }
+        if (col_ok) {
+            // normal-first for a z-face: (rho, rho w, rho u, rho v, E)
+            T st[NS][NC];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const T *rowp = ring + RZ::slot(s - R + q) * (NC * NT) + tid;
+                st[q][0] = rowp[0];
+                st[q][1] = rowp[3 * NT];
+                st[q][2] = rowp[1 * NT];
+                st[q][3] = rowp[2 * NT];
+                st[q][4] = rowp[4 * NT];
+            }
+            T An[NC], Bn[NC];
+            ok = face_rel<T, NC, R>(st, tb, An, Bn) && ok;
+            const T Ac[NC] = {An[0], An[2], An[3], An[1], An[4]};
+            const T Bc[NC] = {Bn[0], Bn[2], Bn[3], Bn[1], Bn[4]};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) Dz[k][c] = Dz[k + 1][c];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                Dz[4][c] = Ac[c] - Ap[c] + Bp[c];
+                Ap[c] = Ac[c];
+                Bp[c] = Bc[c];
+            }
+        }
+        if (out) {
+            const T *urow = ring + RZ::slot(r) * (NC * NT) + tid;
+            T res[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T divz = corrected_divergence<T>(Dz[0][c], Dz[1][c], Dz[2][c], Dz[3][c], Dz[4][c]);
+                const T L = fma(-divz, idx[2], pv[c]);
+                const T un = a.u0_is_stencil ? urow[c * NT] : u0[c];
+                res[c] = stage_epilogue<T>(a, c * cs + cell, L, un, din[c], lov[c], dt);
+            }
+            if (a.rate && a.mode == kModeFinal) {
+                T rx, ry, rz;
+                rates3d<T>(res, tb.gamma, idx, rx, ry, rz);
+                rm[0] = Num<T>::fmax(rm[0], rx);
+                rm[1] = Num<T>::fmax(rm[1], ry);
+                rm[2] = Num<T>::fmax(rm[2], rz);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
+template <typename T, int R, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
+    T rm[3] = {T(0), T(0), T(0)};
+    bool ok = true;
+    const int nz = a.n[2];
+    const long plane = (long)a.n[0] * a.n[1];
+    const long groups = (plane + NT - 1) / NT;
+    const long long total = (long long)groups * nz;
+    long long u = total * blockIdx.x / gridDim.x;
+    const long long uend = total * (blockIdx.x + 1) / gridDim.x;
+    while (u < uend) {
+        const long g = (long)(u / nz);
+        const int z0 = (int)(u - (long long)g * nz);
+        const int z1 = (int)min((long long)nz, z0 + (uend - u));
+        stagez_segment<T, R, NT>(a, tb, g * NT, z0, z1, ring, dt, rm, ok);
+        u += z1 - z0;
+    }
+    finish_block<T>(a, rm[0], rm[1], rm[2], ok);
 }
 
 // ---------------------------------------------------------------------------
