@@ -37,10 +37,13 @@ def flops_per_cell_stage(R: int, ndim: int = 2) -> float:
     return costmodel.flops_per_cell_stage(R, ndim)
 
 
-def hbm_bytes_per_cell_stage(esz: int, nc: int = 4) -> float:
-    """Algorithmic HBM bytes per cell and stage, averaged over the three stages:
-    read the stage input once, write the result once, read U^n in stages 2 and 3."""
-    return esz * nc * (2.0 + 2.0 / 3.0)
+def hbm_bytes_per_cell_stage(esz: int, nc: int = 4, arrays_per_step: float = 14.0) -> float:
+    """Algorithmic HBM bytes per cell and stage of the increment-form SSP-RK3, averaged over
+    the three stages (state-sized arrays moved once each): stage 1 reads U and writes D, V1
+    (3 arrays); stage 2 reads V1, D, U and writes D, V2 (5); stage 3 reads V2, D, U, lo and
+    writes U, lo (6); 14 arrays per step.  In 3D each stage also writes and reads back the
+    x+y part of L and reads its stencil state twice (23 arrays per step)."""
+    return esz * nc * arrays_per_step / 3.0
 
 
 def read_peaks():
@@ -239,6 +242,7 @@ def run_gpu(args):
            "d2h_bytes_per_step": nb, "ms_per_step": e2e_ms / args.steps}
 
     batch = run_batch(args, stream) if args.batch_count > 0 else None
+    extra = run_configs(args, stream) if args.configs else None
 
     if rank != 0:
         return None
@@ -272,6 +276,7 @@ def run_gpu(args):
                          "bytes_per_cell_stage": hbm_bytes_per_cell_stage(4)},
         "e2e": e2e,
         "batch": batch,
+        "configs": extra,
         "gpu_launches": r32["launches_per_step"] * args.steps,
         "clocks": r32["clocks"],
     }
@@ -334,6 +339,74 @@ def run_batch(args, stream):
             "unbatched_value": cells * 3 / (ms_u * 1e-3), "unbatched_ms_per_step": ms_u,
             "speedup_vs_unbatched": ms_u / ms_b, "launches_per_step": 3,
             "unbatched_launches_per_step": 3 * len(insts), "schedule": info, "nonphysical_flag": nonphys}
+
+
+def timed_cfl_run(plan, U, steps, stream, flops_cell, cells, bytes_cell):
+    """`steps` SSP-RK3 steps with the CFL time step kept on the device (fused into the last stage),
+    one step captured in a CUDA graph; returns throughput and roofline fractions."""
+    import torch
+
+    from paper_1808_04960_gb300 import gpweno
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.cfl_dt(U, plan.cfl, dt_dev)
+    s = plan.new_scratch()
+    for _ in range(2):
+        plan.rk3_step(U, s, dt_dev=dt_dev, stream=stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.rk3_step(U, s, dt_dev=dt_dev)
+    launches = gpweno.last_launch_count()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+    per_stage_s = ms * 1e-3 / 3
+    peaks, _ = read_peaks()
+    return {"value": cells * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "launches_per_step": launches, "dt_last": float(dt_dev.item()), "nonphysical_flag": plan.flags(),
+            "alu_frac": flops_cell * cells / per_stage_s / alu_peak,
+            "hbm_frac": bytes_cell * cells / per_stage_s / (peaks.get("hbm_gbs", 6800.0) * 1e9)}
+
+
+def run_configs(args, stream):
+    """The other measured configurations: the 4096^2 seeded four-quadrant Riemann problem (GP-R2,
+    l=12dx, CFL 0.4 from the device each step) and the 3D Mach-3 shock into a 32-mode density field
+    (512^3 by default, GP-R3, CFL 0.4), both FP32."""
+    import torch
+
+    from paper_1808_04960_gb300 import costmodel, gpweno, workloads
+    out = {}
+    n = args.fq_grid
+    U0, m = workloads.four_quadrant(n, seed=3)
+    plan = gpweno.Plan(2, 12.0, U0.shape[1:], m["dx"], m["bc"], dtype="f32", cfl=0.4)
+    U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+    del U0
+    r = timed_cfl_run(plan, U, args.fq_steps, stream, costmodel.flops_per_cell_stage(2, 2), n * n,
+                      hbm_bytes_per_cell_stage(4, 4))
+    r["workload"] = f"four-quadrant Riemann problem {n}x{n} on [0,1]^2, seeded states, outflow, GP-R2, l=12dx, " \
+                    f"sigma=3dx, SSP-RK3, CFL 0.4 (device dt), FP32"
+    out["four_quadrant"] = r
+    del U, plan
+    n3 = args.shock_grid
+    if n3 > 0:
+        U0, m = workloads.shock_turbulence_3d(n3, seed=4)
+        plan = gpweno.Plan(3, 12.0, U0.shape[1:], m["dx"], m["bc"], dtype="f32", cfl=0.4)
+        U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+        del U0
+        r = timed_cfl_run(plan, U, args.shock_steps, stream, costmodel.flops_per_cell_stage(3, 3), n3 ** 3,
+                          hbm_bytes_per_cell_stage(4, 5, 23.0))
+        r["workload"] = f"3D Mach-3 shock into a 32-mode seeded density field, {n3}^3, periodic y/z, " \
+                        f"zero-gradient x, GP-R3, l=12dx, sigma=3dx, SSP-RK3, CFL 0.4 (device dt), FP32"
+        out["shock_turbulence_3d"] = r
+        del U, plan
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(args, dt_full, gpu_compare=True):
@@ -425,6 +498,12 @@ def main():
     ap.add_argument("--dtypes", default="f32,f64", help="comma list; f32 is always first and required")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the four-quadrant 4096^2 and 3D shock-turbulence measurements")
+    ap.add_argument("--fq-grid", type=int, default=4096)
+    ap.add_argument("--fq-steps", type=int, default=100)
+    ap.add_argument("--shock-grid", type=int, default=512)
+    ap.add_argument("--shock-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
