@@ -46,6 +46,22 @@ def hbm_bytes_per_cell_stage(esz: int, nc: int = 4, arrays_per_step: float = 14.
     return esz * nc * arrays_per_step / 3.0
 
 
+def kernel_traffic(key):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary, or None when
+    the kernel sources changed since those counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            entry = json.load(f)[key]
+        h = hashlib.sha256()
+        for src in ("face.cuh", "stage.cuh"):
+            with open(os.path.join(ROOT, "paper_1808_04960_gb300", "csrc", src), "rb") as f:
+                h.update(f.read())
+        return entry["traffic_bytes_per_launch"] if h.hexdigest() == entry["kernel_sources_sha256"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,7 +283,9 @@ def run_gpu(args):
                  if "f64" in results else None),
         "accuracy": acc,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": (kernel_traffic(f"stage2d_kernel<float,{R},256> vortex{n}")
+                                 if args.graph and n == 1024 and R == 2 else None),
                      "kernel": f"stage2d_kernel<float,{R},256>",
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "flops_per_cell_stage": flops_per_cell_stage(R)},
