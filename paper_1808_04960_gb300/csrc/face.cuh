@@ -18,10 +18,12 @@
 //     alpha = max(|u_n|+c) over both states (Eq. riemann_prob).
 // Stencil values arrive conserved and "normal-first": (rho, m_normal, m_tangential..., E).
 //
-// Nonlinear weights use the ratio form omega_m = gamma_m r_m^p / sum_s gamma_s r_s^p
-// with r_m = b_min / b_m, b_m = eps + beta_m.  It equals Eq. weights
-// exactly in real arithmetic and keeps (eps + beta)^p from underflowing in
-// FP32 when beta -> 0 (eps = 1e-36 squared is below the FP32 range).
+// Nonlinear weights follow Eq. weights literally, omega_m ~ gamma_m / (eps + beta_m)^p,
+// with one reciprocal per smoothness window shared by both sides of the face.
+// In FP32 eps + beta is kept >= 1e-18 (eps rescaled out of the FP32 denormal
+// range: (1e-36)^-2 would overflow); this changes omega only where every
+// affected window holds data below ~1e-9, i.e. below FP32 resolution of the
+// state.  FP64 uses eps = 1e-36 exactly.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -56,6 +58,11 @@ struct Num<float> {
     static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
     static __device__ __forceinline__ float fmax(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float fmin(float a, float b) { return fminf(a, b); }
+    // lower bound of eps + beta in FP32, so that (eps + beta)^-2 stays within range
+    static __device__ __forceinline__ float eps_floor() { return 1e-18f; }
+    // uncontracted multiply / add (never fused into an FMA, so every kernel rounds alike)
+    static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 };
 
 template <>
@@ -66,6 +73,9 @@ struct Num<double> {
     static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
     static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
     static __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
+    static __device__ __forceinline__ double eps_floor() { return 0.0; }
+    static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 };
 
 // Weight tables of one plan in the arithmetic type.  Passed by value as a
@@ -86,25 +96,6 @@ struct FaceTables {
     T gamma;              // ratio of specific heats
     int p;                // WENO power, 1 or 2
 };
-
-// Nonlinear GP-WENO combination for one side: candidates q[m], beta windows b[m]
-// (already eps + beta), linear weights g[m].  Ratio form of Eq. weights.
-template <typename T, int R>
-__device__ __forceinline__ T weno_combine(const T (&q)[R + 1], const T (&b)[R + 1], const T (&g)[R + 1], int p)
-{
-    T bmin = b[0];
-#pragma unroll
-    for (int m = 1; m <= R; ++m) bmin = Num<T>::fmin(bmin, b[m]);
-    T num = T(0), den = T(0);
-#pragma unroll
-    for (int m = 0; m <= R; ++m) {
-        T r = bmin * Num<T>::rcp(b[m]);
-        T w = g[m] * (p == 2 ? r * r : r);
-        num = fma(w, q[m], num);
-        den += w;
-    }
-    return num * Num<T>::rcp(den);
-}
 
 // Primitive reference state of the "cell-relative" evaluation (normal-first order).
 template <typename T, int NC>
@@ -269,7 +260,13 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
         for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : lrow(kk, dV[j]);
 
         // --- smoothness indicators on the R+2 windows d[w..w+R] --------
-        T b[R + 2];
+        // P_h . f_w = P_h . d_w + f_c sum_j P_hj for the symmetric rows; the
+        // f_c term is the same for every window.
+        T pf[S];
+#pragma unroll
+        for (int h = 0; h < S; ++h) pf[h] = (h % 2 == 0) ? tb.Psum[h] * fc : T(0);
+        // xw_w = (eps + beta_w)^-p, shared by the two sides of the face
+        T xw[R + 2];
 #pragma unroll
         for (int w = 0; w < R + 2; ++w) {
             T ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
@@ -284,7 +281,7 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             for (int h = 0; h < S; ++h) {
                 T dot;
                 if (h % 2 == 0) {
-                    dot = tb.Psum[h] * fc;
+                    dot = pf[h];
                     if (S % 2 == 1 && w + HALF != R) dot = fma(tb.Ph[h][HALF], d[w + HALF], dot);
 #pragma unroll
                     for (int j = 0; j < HALF; ++j) dot = fma(tb.Ph[h][j], ps[j], dot);
@@ -295,10 +292,12 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
                 }
                 beta = fma(dot, dot, beta);
             }
-            b[w] = tb.eps + beta;
+            const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(tb.eps, beta), Num<T>::eps_floor()));
+            xw[w] = tb.p == 2 ? Num<T>::mul_rn(x, x) : x;   // (eps + beta)^-p
         }
-        // --- candidates relative to the centre cells, both sides ---------
-        T cl[R + 1], cr_[R + 1], bl[R + 1], br[R + 1];
+        // --- candidates relative to the centre cells and nonlinear weights ---
+        // omega_m ~ gamma_m (eps + beta_m)^-p  (Eq. weights); sum_m omega_m = 1 is used exactly.
+        T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
 #pragma unroll
         for (int m = 0; m <= R; ++m) {
             T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
@@ -307,13 +306,15 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
                 if (m + j != R) sl = fma(tb.wl[m][j], d[m + j], sl);
                 if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
             }
-            cl[m] = sl;
-            cr_[m] = sr;
-            bl[m] = b[m];
-            br[m] = b[m + 1];
+            const T yl = Num<T>::mul_rn(tb.gl[m], xw[m]);
+            const T yr = Num<T>::mul_rn(tb.gr[m], xw[m + 1]);
+            numL = fma(yl, sl, numL);
+            denL = Num<T>::add_rn(denL, yl);
+            numR = fma(yr, sr, numR);
+            denR = Num<T>::add_rn(denR, yr);
         }
-        dqL[kk] = weno_combine<T, R>(cl, bl, tb.gl, tb.p);              // q_L - L V_s
-        dqR[kk] = weno_combine<T, R>(cr_, br, tb.gr, tb.p) - d[R + 1];  // q_R - L V_{s+1}
+        dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
+        dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}
     }
 
     // --- back-projection: primitive states relative to cell s -------------
