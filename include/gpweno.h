@@ -74,7 +74,10 @@ typedef struct {
  *   cfl            if > 0, gpweno_rk3_step with a dt_dev pointer also writes
  *                  the next step's dt = cfl / sum_d max(|u_d|+c)/dx_d of the
  *                  new state into *dt_dev (fused into the last stage).
- *   flux_form      0 = FD-Prim with local Lax-Friedrichs face flux (only value). */
+ *   flux_form      face flux of Eq. riemann_prob on the GP-WENO states:
+ *                  0 = local Lax-Friedrichs (default), 1 = HLLC with Einfeldt
+ *                  wave speeds from the Roe average (the paper's default
+ *                  solver, Section 7). */
 typedef struct {
     double sigma_over_dx;
     double eps;

@@ -54,7 +54,7 @@ class _Cfg(ctypes.Structure):
                 ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("R", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("wl", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("wr", ctypes.c_void_p),
-                ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p)]
+                ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int)]
 
 
 def _load():
@@ -76,6 +76,8 @@ def _load():
             lib.oracle_roe.restype = ctypes.c_int
             lib.oracle_gp_weno.argtypes = [P, dp, ctypes.c_int]
             lib.oracle_gp_weno.restype = ctypes.c_double
+            lib.oracle_hllc.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+            lib.oracle_hllc.restype = None
             lib.oracle_corrected_flux.argtypes = [dp]
             lib.oracle_corrected_flux.restype = ctypes.c_double
             _lib = lib
@@ -96,7 +98,7 @@ class Oracle:
     """
 
     def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
-                 gamma=1.4, eps=1e-36, p=2):
+                 gamma=1.4, eps=1e-36, p=2, flux="lf"):
         self.lib = _load()
         shape = tuple(int(s) for s in shape)
         self.ndim = len(shape)
@@ -119,6 +121,7 @@ class Oracle:
         c.eps = float(eps)
         c.p = int(p)
         c.wl, c.gl, c.wr, c.gr, c.Kinv = [a.ctypes.data for a in self._keep]
+        c.flux = {"lf": 0, "hllc": 1}[flux]
         self.cfg = c
         self.R = int(R)
         self.gamma = float(gamma)
@@ -187,6 +190,16 @@ def roe_eigensystem(uL, uR, gamma=1.4):
     if not lib.oracle_roe(nc, float(gamma), _ptr(uL), _ptr(uR), _ptr(roe), _ptr(Rm), _ptr(Lm)):
         raise FloatingPointError("non-physical Roe state")
     return roe, Rm, Lm
+
+
+def hllc(uL, uR, uroe, croe, gamma=1.4):
+    """HLLC flux of two conserved normal-first states (Einfeldt speeds from the given Roe values)."""
+    lib = _load()
+    uL = np.ascontiguousarray(uL, dtype=np.float64)
+    uR = np.ascontiguousarray(uR, dtype=np.float64)
+    F = np.zeros(uL.shape[0])
+    lib.oracle_hllc(uL.shape[0], float(gamma), _ptr(uL), _ptr(uR), float(uroe), float(croe), _ptr(F))
+    return F
 
 
 def corrected_flux(F5):

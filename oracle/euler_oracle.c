@@ -16,7 +16,8 @@
  *     omega_m = gamma_m/(eps+beta_m)^p normalised (Eq. weights), combination
  *     q = sum omega_m q^m (Eq. weight_sum);
  *   - the face flux F_{i+1/2} = RP(U^L, U^R) (Eq. riemann_prob) taken as the
- *     local Lax-Friedrichs (Rusanov) flux;
+ *     local Lax-Friedrichs (Rusanov) flux, or the HLLC flux that the paper
+ *     uses by default (Section 7);
  *   - the high-order correction f^ = F + alpha D^2F + beta D^4F with
  *     alpha = -1/24, beta = 3/640 on neighbouring face fluxes (Eqs. numFlux_cor,
  *     FD-ders);
@@ -58,6 +59,7 @@ typedef struct {
     const double *wr;  /* [(R+1)][(R+1)] sub-stencil weights, prediction at x* = -1/2 */
     const double *gr;  /* [(R+1)] linear weights at x* = -1/2 */
     const double *Kinv;/* [(R+1)][(R+1)] inverse of K_m built with sigma */
+    int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC */
 } oracle_cfg;
 
 static long ncells(const oracle_cfg *c) { return (long)c->n[0] * c->n[1] * c->n[2]; }
@@ -195,6 +197,43 @@ static double gp_weno(const oracle_cfg *c, const double *f, const double *w, con
     return out;
 }
 
+/* HLLC flux (Toro's three-wave approximate Riemann solver) of two conserved
+ * normal-first states, with the wave speeds of Einfeldt from the Roe average:
+ * S_L = min(u_L - c_L, u_roe - c_roe), S_R = max(u_R + c_R, u_roe + c_roe),
+ * contact speed S* from the momentum jump, star states
+ * U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S*, v_K, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))). */
+static void hllc_flux(const double *uL, const double *uR, int nc, double g, double uroe, double croe, double *F)
+{
+    int E = nc - 1;
+    double rL = uL[0], rR = uR[0];
+    double vL = uL[1] / rL, vR = uR[1] / rR;
+    double pL = pressure(uL, nc, g), pR = pressure(uR, nc, g);
+    double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    double SL = fmin(vL - cL, uroe - croe), SR = fmax(vR + cR, uroe + croe);
+    double Ss = (pR - pL + rL * vL * (SL - vL) - rR * vR * (SR - vR)) / (rL * (SL - vL) - rR * (SR - vR));
+    double fL[OR_MAXC], fR[OR_MAXC];
+    normal_flux(uL, nc, g, fL);
+    normal_flux(uR, nc, g, fR);
+    if (SL >= 0.0) {
+        for (int a = 0; a < nc; ++a) F[a] = fL[a];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int a = 0; a < nc; ++a) F[a] = fR[a];
+        return;
+    }
+    const double *uK = Ss >= 0.0 ? uL : uR;
+    const double *fK = Ss >= 0.0 ? fL : fR;
+    double rK = uK[0], vK = uK[1] / rK, pK = Ss >= 0.0 ? pL : pR, SK = Ss >= 0.0 ? SL : SR;
+    double chi = rK * (SK - vK) / (SK - Ss);
+    double us[OR_MAXC];
+    us[0] = chi;
+    us[1] = chi * Ss;
+    for (int a = 2; a < E; ++a) us[a] = chi * uK[a] / rK;
+    us[E] = chi * (uK[E] / rK + (Ss - vK) * (Ss + pK / (rK * (SK - vK))));
+    for (int a = 0; a < nc; ++a) F[a] = fK[a] + SK * (us[a] - uK[a]);
+}
+
 /* Face flux F between cells s and s+1 along dimension d, at transverse
  * position (t1, t2) meaning the other two cell indices in natural order.
  * Writes nc values (natural component order).  Returns 0 on a non-physical
@@ -250,14 +289,20 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
     to_conserved(vR, nc, c->gamma, uR);
     double pL = pressure(uL, nc, c->gamma), pR = pressure(uR, nc, c->gamma);
     if (!(uL[0] > 0.0) || !(uR[0] > 0.0) || !(pL > 0.0) || !(pR > 0.0)) return 0;
-    double cL = sqrt(c->gamma * pL / uL[0]), cR = sqrt(c->gamma * pR / uR[0]);
-    double aL = fabs(uL[1] / uL[0]) + cL, aR = fabs(uR[1] / uR[0]) + cR;
-    double alpha = aL > aR ? aL : aR;
-    double fL[OR_MAXC], fR[OR_MAXC];
-    normal_flux(uL, nc, c->gamma, fL);
-    normal_flux(uR, nc, c->gamma, fR);
+    double Fn[OR_MAXC];
+    if (c->flux == 1) {
+        hllc_flux(uL, uR, nc, c->gamma, roe[1], roe[nc], Fn);
+    } else {
+        double cL = sqrt(c->gamma * pL / uL[0]), cR = sqrt(c->gamma * pR / uR[0]);
+        double aL = fabs(uL[1] / uL[0]) + cL, aR = fabs(uR[1] / uR[0]) + cR;
+        double alpha = aL > aR ? aL : aR;
+        double fL[OR_MAXC], fR[OR_MAXC];
+        normal_flux(uL, nc, c->gamma, fL);
+        normal_flux(uR, nc, c->gamma, fR);
+        for (int a = 0; a < nc; ++a) Fn[a] = 0.5 * (fL[a] + fR[a]) - 0.5 * alpha * (uR[a] - uL[a]);
+    }
     for (int a = 0; a < nc; ++a) {
-        Fout[perm[a]] = 0.5 * (fL[a] + fR[a]) - 0.5 * alpha * (uR[a] - uL[a]);
+        Fout[perm[a]] = Fn[a];
         if (uLout) uLout[perm[a]] = uL[a];
         if (uRout) uRout[perm[a]] = uR[a];
     }
@@ -357,6 +402,13 @@ double oracle_max_rate(const oracle_cfg *c, const double *U)
         tot += mx / c->dx[d];
     }
     return tot;
+}
+
+/* HLLC flux of two conserved normal-first states with given Roe velocity and
+ * sound speed, exposed for unit tests. */
+void oracle_hllc(int nc, double g, const double *uL, const double *uR, double uroe, double croe, double *F)
+{
+    hllc_flux(uL, uR, nc, g, uroe, croe, F);
 }
 
 /* Single face, exposed for unit tests: Riemann states and flux at the face

@@ -99,8 +99,8 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
         set_error("eps=%g must be positive (and a normal FP32 number for dtype F32)", o.eps);
         return GPWENO_ERR_ARG;
     }
-    if (o.flux_form != 0) {
-        set_error("flux_form=%d: only 0 (FD-Prim, Lax-Friedrichs) is available", o.flux_form);
+    if (o.flux_form != 0 && o.flux_form != 1) {
+        set_error("flux_form=%d: 0 (local Lax-Friedrichs) or 1 (HLLC)", o.flux_form);
         return GPWENO_ERR_ARG;
     }
     long ncell = 1;

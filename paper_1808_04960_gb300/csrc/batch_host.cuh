@@ -125,7 +125,8 @@ gpweno_status build_batch_T(gpweno_plan b)
         int idx = -1;
         for (int q = 0; q < (int)rv.size(); ++q)
             if (rv[q]->ell == p->ell && rv[q]->opts.sigma_over_dx == p->opts.sigma_over_dx &&
-                rv[q]->gamma == p->gamma && rv[q]->opts.eps == p->opts.eps && rv[q]->opts.p == p->opts.p)
+                rv[q]->gamma == p->gamma && rv[q]->opts.eps == p->opts.eps && rv[q]->opts.p == p->opts.p &&
+                rv[q]->opts.flux_form == p->opts.flux_form)
                 idx = q;
         if (idx < 0) {
             if ((int)rv.size() >= kBatchMaxSets) {

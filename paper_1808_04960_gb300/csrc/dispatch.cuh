@@ -33,6 +33,7 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
     t.eps = (T)p->opts.eps;
     t.gamma = (T)p->gamma;
     t.p = p->opts.p;
+    t.flux = p->opts.flux_form;
     return t;
 }
 

@@ -13,9 +13,10 @@
 //     smoothness indicators beta = sum_h (P_h . f_m)^2 (Eq. beta-eigen, the
 //     R+2 windows shared by both sides), nonlinear weights (Eq. weights) and
 //     their combination (Eq. weight_sum);
-//   - back-projection to conserved states U^L, U^R and the local
-//     Lax-Friedrichs flux F = (F(U^L)+F(U^R))/2 - alpha (U^R-U^L)/2 with
-//     alpha = max(|u_n|+c) over both states (Eq. riemann_prob).
+//   - back-projection to the Riemann states U^L, U^R and the face flux of
+//     Eq. riemann_prob: local Lax-Friedrichs, F = (F(U^L)+F(U^R))/2 -
+//     alpha (U^R-U^L)/2 with alpha = max(|u_n|+c) over both states, or HLLC
+//     (the paper's default solver, Section 7) with Einfeldt wave speeds.
 // Stencil values arrive conserved and "normal-first": (rho, m_normal, m_tangential..., E).
 //
 // Nonlinear weights follow Eq. weights literally, omega_m ~ gamma_m / (eps + beta_m)^p,
@@ -95,6 +96,7 @@ struct FaceTables {
     T eps;                // WENO epsilon
     T gamma;              // ratio of specific heats
     int p;                // WENO power, 1 or 2
+    int flux;             // face flux: 0 local Lax-Friedrichs, 1 HLLC
 };
 
 // Primitive reference state of the "cell-relative" evaluation (normal-first order).
@@ -115,10 +117,11 @@ struct PrimRef {
 //   k   = rho|u|^2 - rho_s|u_s|^2 = sum_a (g_a u_a + rho_s u_s,a w_a)
 //   E'  = w_p/(gamma-1) + k/2
 //   G   = (g_n,  g_n u_n + m_s,n w_n + w_p,  g_n u_t + m_s,n w_t,  w_n (E+p)_s + u_n (E' + w_p)).
-// Returns false if rho <= 0 or p <= 0 (or NaN); speed = |u_n| + c of the full state.
+// Returns false if rho <= 0 or p <= 0 (or NaN); un and cs are the normal velocity and
+// the sound speed of the full state.
 template <typename T, int NC>
 __device__ __forceinline__ bool prim_pert(const PrimRef<T, NC> &r, const T (&w)[NC], T gam, T igm1, T (&G)[NC],
-                                          T (&cw)[NC], T &speed)
+                                          T (&cw)[NC], T &un, T &cs)
 {
     constexpr int NV = NC - 2, E = NC - 1;
     const T rho = r.rho + w[0];
@@ -141,7 +144,8 @@ __device__ __forceinline__ bool prim_pert(const PrimRef<T, NC> &r, const T (&w)[
     for (int a = 1; a < NV; ++a) G[1 + a] = fma(g[0], u[a], r.mn * w[1 + a]);
     G[E] = fma(w[1], r.hp, u[0] * (ep + w[E]));
     const T pr = r.p + w[E];
-    speed = Num<T>::fabs(u[0]) + Num<T>::sqrt(Num<T>::fmax(gam * pr * Num<T>::rcp(rho), T(1e-30)));
+    un = u[0];
+    cs = Num<T>::sqrt(Num<T>::fmax(gam * pr * Num<T>::rcp(rho), T(1e-30)));
     return (rho > T(0)) && (pr > T(0));
 }
 
@@ -331,17 +335,58 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
     wL[E] = c2 * (dqL[0] + dqL[E]);
     wR[E] = fma(c2, dqR[0] + dqR[E], dV[R + 1][E]);
 
-    // --- Lax-Friedrichs flux relative to F(U_s), and F(U_{s+1}) - F(U_s) ----
-    T GL[NC], GR[NC], cL[NC], cR[NC], cB[NC], sL, sR, sB;
-    ok = prim_pert<T, NC>(ref, wL, tb.gamma, igm1, GL, cL, sL) && ok;
-    ok = prim_pert<T, NC>(ref, wR, tb.gamma, igm1, GR, cR, sR) && ok;
+    // --- face flux relative to F(U_s), and F(U_{s+1}) - F(U_s) ---------------
+    T GL[NC], GR[NC], cL[NC], cR[NC], cB[NC], uL, uR, aL, aR, uB, aB;
+    ok = prim_pert<T, NC>(ref, wL, tb.gamma, igm1, GL, cL, uL, aL) && ok;
+    ok = prim_pert<T, NC>(ref, wR, tb.gamma, igm1, GR, cR, uR, aR) && ok;
     T dn[NC];
 #pragma unroll
     for (int a = 0; a < NC; ++a) dn[a] = dV[R + 1][a];
-    ok = prim_pert<T, NC>(ref, dn, tb.gamma, igm1, B, cB, sB) && ok;
-    const T alpha = Num<T>::fmax(sL, sR);
+    ok = prim_pert<T, NC>(ref, dn, tb.gamma, igm1, B, cB, uB, aB) && ok;
+    if (tb.flux == 1) {
+        // HLLC with Einfeldt speeds from the Roe average.  The contact speed enters only
+        // through S* - u_K = (dp - rho_K' (S_K' - u_K') du) / D (K' the other side), formed
+        // from the small differences dp = p_R - p_L, du = u_R - u_L, so the star states
+        // U*_K - U_K stay accurate increments.
+        const T rhoL = ref.rho + wL[0], rhoR = ref.rho + wR[0];
+        const T pLf = ref.p + wL[E], pRf = ref.p + wR[E];
+        const T SL = Num<T>::fmin(uL - aL, vel[0] - c), SR = Num<T>::fmax(uR + aR, vel[0] + c);
+        const T mL = rhoL * (SL - uL), mR = rhoR * (SR - uR);
+        const T iD = Num<T>::rcp(mL - mR);
+        const T dp = wR[E] - wL[E], du = wR[1] - wL[1];
+        const T sL = (dp - mR * du) * iD;   // S* - u_L
+        const T sR = (dp - mL * du) * iD;   // S* - u_R
+        const T Ss = uL + sL;
+        const T Es = ref.hp - ref.p;
+        auto star = [&](const T (&w)[NC], const T (&cw)[NC], T rho, T pK, T mK, T SK, T sK, T (&dU)[NC]) {
+            // U*_K - U_K with chi = rho_K (S_K - u_K) / (S_K - S*), chi - 1 = (S* - u_K) / (S_K - S*)
+            const T q = Num<T>::rcp(mK * Num<T>::rcp(rho) - sK);   // 1 / (S_K - S*)
+            const T chi1 = sK * q;
+            dU[0] = rho * chi1;
+            dU[1] = rho * fma(chi1, Ss, sK);
 #pragma unroll
-    for (int a = 0; a < NC; ++a) A[a] = T(0.5) * ((GL[a] + GR[a]) - alpha * (cR[a] - cL[a]));
+            for (int a = 2; a < E; ++a) dU[a] = rho * (ref.u[a - 1] + w[a]) * chi1;
+            const T EK = Es + cw[E];
+            // chi rho_K (S* - u_K)(S* + p_K / (rho_K (S_K - u_K))), with chi rho_K = m_K q
+            dU[E] = fma(chi1, EK, mK * q * sK * (Ss + pK * Num<T>::rcp(mK)));
+        };
+        T dUL[NC], dUR[NC];
+        star(wL, cL, rhoL, pLf, mL, SL, sL, dUL);
+        star(wR, cR, rhoR, pRf, mR, SR, sR, dUR);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            T f;
+            if (SL >= T(0)) f = GL[a];
+            else if (SR <= T(0)) f = GR[a];
+            else if (Ss >= T(0)) f = fma(SL, dUL[a], GL[a]);
+            else f = fma(SR, dUR[a], GR[a]);
+            A[a] = f;
+        }
+    } else {
+        const T alpha = Num<T>::fmax(Num<T>::fabs(uL) + aL, Num<T>::fabs(uR) + aR);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) A[a] = T(0.5) * ((GL[a] + GR[a]) - alpha * (cR[a] - cL[a]));
+    }
     return ok;
 }
 

@@ -133,7 +133,7 @@ class Plan:
     """
 
     def __init__(self, R, ell_over_dx, shape, dx, bc, gamma=1.4, sigma_over_dx=3.0, eps=1e-36, p=2,
-                 dtype="f32", cfl=0.0):
+                 dtype="f32", cfl=0.0, flux="lf"):
         import torch
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
@@ -158,6 +158,7 @@ class Plan:
         opts.p = int(p)
         opts.dtype = F32 if dtype == "f32" else F64
         opts.cfl = float(cfl)
+        opts.flux_form = {"lf": 0, "hllc": 1}[flux]
         h = ctypes.c_void_p()
         _check(self.lib.gpweno_plan_create(ctypes.byref(h), self.R, float(ell_over_dx), ctypes.byref(dims),
                                            float(gamma), ctypes.byref(opts)), "gpweno_plan_create")

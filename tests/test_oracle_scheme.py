@@ -290,3 +290,81 @@ def test_convergence_against_table1(R, ns):
         order = math.log(errs[k - 1] / errs[k], 2)
         ref_order = tab[ns[k]][2 + 2 * (R - 1)]
         assert abs(order - ref_order) < 0.5, (ns[k], order, ref_order)
+
+
+# ---------------------------------------------------------------------------
+# HLLC face flux (the paper's default solver, Section 7)
+
+def _roe_uc(uL, uR, g=1.4):
+    roe, _, _ = oracle.roe_eigensystem(uL, uR, g)
+    nc = len(uL)
+    return roe[1], roe[nc]
+
+
+@pytest.mark.parametrize("nc", [3, 4, 5])
+def test_hllc_consistency_and_supersonic(nc):
+    """F(U, U) = F(U); fully supersonic states take the upwind physical flux."""
+    g = 1.4
+    rng = np.random.default_rng(40 + nc)
+    for _ in range(5):
+        u = rand_state(rng, nc)
+        ur, cr = _roe_uc(u, u)
+        np.testing.assert_allclose(oracle.hllc(u, u, ur, cr), euler_flux(u, g), rtol=1e-13, atol=1e-13)
+    # supersonic to the right: u - c > 0 on both sides and at the Roe state
+    uL = W.conserved(np.array(1.0), [np.array(3.0)] + [np.array(0.1)] * (nc - 3), np.array(1.0), g)
+    uR = W.conserved(np.array(0.8), [np.array(2.9)] + [np.array(-0.2)] * (nc - 3), np.array(0.9), g)
+    ur, cr = _roe_uc(uL, uR)
+    np.testing.assert_allclose(oracle.hllc(uL, uR, ur, cr), euler_flux(uL, g), rtol=1e-13)
+
+
+def test_hllc_resolves_stationary_and_moving_contacts():
+    """An isolated contact (equal u and p, different rho and v) is a single HLLC wave: the flux is
+    the exact upwind flux of the contact (mass flux rho*u of the upwind side, zero if u = 0)."""
+    g = 1.4
+    for u in (0.0, 0.4, -0.3):
+        uL = W.conserved(np.array(1.0), [np.array(u), np.array(0.3)], np.array(1.0), g)
+        uR = W.conserved(np.array(0.2), [np.array(u), np.array(-0.5)], np.array(1.0), g)
+        ur, cr = _roe_uc(uL, uR)
+        F = oracle.hllc(uL, uR, ur, cr)
+        up = uL if u >= 0 else uR
+        np.testing.assert_allclose(F, euler_flux(up, g), rtol=1e-12, atol=1e-13)
+
+
+def test_hllc_mirror_symmetry():
+    """Reflecting x -> -x maps F(UL, UR) to the mirrored flux of (mirror UR, mirror UL)."""
+    g = 1.4
+    rng = np.random.default_rng(9)
+    M = np.diag([1.0, -1.0, 1.0, 1.0])
+    for _ in range(10):
+        uL, uR = rand_state(rng, 4), rand_state(rng, 4)
+        ur, cr = _roe_uc(uL, uR)
+        F = oracle.hllc(uL, uR, ur, cr)
+        mL, mR = M @ uR, M @ uL
+        ur2, cr2 = _roe_uc(mL, mR)
+        F2 = oracle.hllc(mL, mR, ur2, cr2)
+        np.testing.assert_allclose(-(M @ F2), F, rtol=1e-12, atol=1e-12)
+
+
+def test_hllc_scheme_free_stream_and_order():
+    """The whole scheme with HLLC preserves free streams exactly and keeps the Table 1 orders."""
+    rng = np.random.default_rng(2)
+    u0 = rand_state(rng, 4)
+    U = np.empty((4, 11, 13))
+    for a in range(4):
+        U[a] = u0[a]
+    o = oracle.Oracle((11, 13), (0.1, 0.1), (("outflow", "outflow"),) * 2, R=2, flux="hllc")
+    assert np.abs(o.rhs(U)).max() == 0.0
+    errs = []
+    for n in (50, 100):
+        Ug, m = W.gaussian_1d(n)
+        oo = oracle.Oracle((n,), m["dx"], m["bc"], R=2, ell_over_dx=0.1 * n, gamma=m["gamma"], flux="hllc")
+        dx = m["dx"][0]
+        dt = 0.4 * dx / 2.3 * (dx / (1.0 / 25)) ** (5 / 3.0 - 1.0)
+        steps = int(math.ceil(1.0 / dt))
+        Un = oo.run(Ug, 1.0 / steps, steps)
+        Ue, _ = W.gaussian_1d(n, t=1.0)
+        errs.append(np.abs(Un[0] - Ue[0]).mean())
+    tab = _table1()
+    order = math.log(errs[0] / errs[1], 2)
+    assert abs(order - tab[100][4]) < 0.5, (errs, order)
+    assert tab[100][3] / 2.5 < errs[1] < tab[100][3] * 2.5
