@@ -54,7 +54,8 @@ class _Cfg(ctypes.Structure):
                 ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("R", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("wl", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("wr", ctypes.c_void_p),
-                ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int)]
+                ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int),
+                ("beta_mean", ctypes.c_int)]
 
 
 def _load():
@@ -98,13 +99,13 @@ class Oracle:
     """
 
     def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
-                 gamma=1.4, eps=1e-36, p=2, flux="lf"):
+                 gamma=1.4, eps=1e-36, p=2, flux="lf", beta_mean=False, candidates="gp"):
         self.lib = _load()
         shape = tuple(int(s) for s in shape)
         self.ndim = len(shape)
         self.shape = shape
         self.nc = self.ndim + 2
-        t = gp_tables.scheme_tables(R, ell_over_dx, sigma_over_dx)
+        t = gp_tables.scheme_tables(R, ell_over_dx, sigma_over_dx, poly=(candidates == "poly"))
         self.tables = t
         self._keep = [np.ascontiguousarray(t[k], dtype=np.float64) for k in ("wl", "gl", "wr", "gr", "Kinv")]
         c = _Cfg()
@@ -122,6 +123,7 @@ class Oracle:
         c.p = int(p)
         c.wl, c.gl, c.wr, c.gr, c.Kinv = [a.ctypes.data for a in self._keep]
         c.flux = {"lf": 0, "hllc": 1}[flux]
+        c.beta_mean = 1 if beta_mean else 0
         self.cfg = c
         self.R = int(R)
         self.gamma = float(gamma)

@@ -60,6 +60,7 @@ typedef struct {
     const double *gr;  /* [(R+1)] linear weights at x* = -1/2 */
     const double *Kinv;/* [(R+1)][(R+1)] inverse of K_m built with sigma */
     int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC */
+    int beta_mean;     /* 0 = zero-mean GP smoothness indicators (the paper's choice), 1 = mean f_centre */
 } oracle_cfg;
 
 static long ncells(const oracle_cfg *c) { return (long)c->n[0] * c->n[1] * c->n[2]; }
@@ -186,9 +187,12 @@ static double gp_weno(const oracle_cfg *c, const double *f, const double *w, con
         const double *fm = f + m;
         double qm = 0.0;
         for (int j = 0; j < S; ++j) qm += w[m * S + j] * fm[j];              /* Eq. candidate_interp */
-        double beta = 0.0;                                                     /* Eq. gp-smooth */
+        /* Eq. gp-smooth; with a non-zero mean the data are taken relative to the
+         * centre value f_i of the stencil (Section 3.3, the variant of Section 7.1) */
+        double mean = c->beta_mean ? f[R] : 0.0;
+        double beta = 0.0;
         for (int a = 0; a < S; ++a)
-            for (int b = 0; b < S; ++b) beta += fm[a] * c->Kinv[a * S + b] * fm[b];
+            for (int b = 0; b < S; ++b) beta += (fm[a] - mean) * c->Kinv[a * S + b] * (fm[b] - mean);
         q[m] = qm;
         wt[m] = gam[m] / pow(c->eps + beta, (double)c->p);                     /* Eq. weights */
         wsum += wt[m];

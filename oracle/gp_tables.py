@@ -165,15 +165,29 @@ def m_matrix(w_sub, R):
     return M
 
 
+def lagrange_weights(points, xs):
+    """Lagrange basis values l_j(x*) = prod_{k != j} (x* - x_k) / (x_j - x_k) (polynomial interpolation)."""
+    with decimal.localcontext(_ctx()):
+        out = []
+        for j, xj in enumerate(points):
+            v = Decimal(1)
+            for k, xk in enumerate(points):
+                if k != j:
+                    v *= (xs - xk) / (xj - xk)
+            out.append(v)
+        return out
+
+
 @lru_cache(maxsize=None)
-def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str):
+def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str, poly: bool = False):
     ell, sigma, xs = Decimal(ell_s), Decimal(sigma_s), Decimal(xs_s)
     big = [Decimal(j) for j in range(-R, R + 1)]
-    w_big = gp_weights(big, xs, ell)
+    weights = lagrange_weights if poly else (lambda pts, x: gp_weights(pts, x, ell))
+    w_big = weights(big, xs)
     w_sub = []
     for m in range(R + 1):
         pts = [Decimal(j) for j in range(-R + m, m + 1)]
-        w_sub.append(gp_weights(pts, xs, ell))
+        w_sub.append(weights(pts, xs))
     M = m_matrix(w_sub, R)
     gam = least_squares(M, w_big)
     # smoothness-indicator covariance: any sub-stencil (they are all identical, Eq. beta-eigen text)
@@ -185,9 +199,13 @@ def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str):
                 lam_sigma=lam, V_sigma=V, K_ell=covariance(big, ell))
 
 
-def tables_decimal(R: int, ell_over_dx, sigma_over_dx, xstar):
-    """Decimal tables (see module docstring) for one prediction point x* in units of Delta."""
-    return _tables_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)))
+def tables_decimal(R: int, ell_over_dx, sigma_over_dx, xstar, poly=False):
+    """Decimal tables (see module docstring) for one prediction point x* in units of Delta.
+    poly=True: polynomial (Lagrange) candidate and big-stencil weights instead of the GP
+    weights -- the WENO-GP hybrid of the paper's WENO-JS comparison (GP smoothness
+    indicators on polynomial candidates); the linear weights then solve Eq. gamm-system
+    for those weights."""
+    return _tables_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)), bool(poly))
 
 
 def _f64(x):
@@ -196,19 +214,19 @@ def _f64(x):
     return float(x)
 
 
-def tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5) -> dict:
+def tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5, poly: bool = False) -> dict:
     """The same tables rounded to float64 numpy arrays."""
-    t = tables_decimal(R, ell_over_dx, sigma_over_dx, xstar)
+    t = tables_decimal(R, ell_over_dx, sigma_over_dx, xstar, poly)
     out = {k: _f64(v) for k, v in t.items()}
     out["R"] = int(R)
     return out
 
 
-def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0) -> dict:
+def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, poly: bool = False) -> dict:
     """Everything the per-face oracle needs: left-state tables (x* = +1/2 from
     the stencil of cell i), right-state tables (x* = -1/2 from the stencil of
     cell i+1, computed directly, not by reversal) and K_m(sigma)^{-1}."""
-    tl = tables(R, ell_over_dx, sigma_over_dx, 0.5)
-    tr = tables(R, ell_over_dx, sigma_over_dx, -0.5)
+    tl = tables(R, ell_over_dx, sigma_over_dx, 0.5, poly)
+    tr = tables(R, ell_over_dx, sigma_over_dx, -0.5, poly)
     return dict(R=int(R), wl=tl["w_sub"], gl=tl["gamma"], wr=tr["w_sub"], gr=tr["gamma"],
                 Kinv=tl["Kinv_sigma"], w_big_l=tl["w_big"], w_big_r=tr["w_big"])

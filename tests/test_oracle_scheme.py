@@ -368,3 +368,83 @@ def test_hllc_scheme_free_stream_and_order():
     order = math.log(errs[0] / errs[1], 2)
     assert abs(order - tab[100][4]) < 0.5, (errs, order)
     assert tab[100][3] / 2.5 < errs[1] < tab[100][3] * 2.5
+
+
+# ---------------------------------------------------------------------------
+# Variants: non-zero-mean smoothness indicators and the polynomial-candidate hybrid
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_nonzero_mean_beta_is_shift_invariant(R):
+    """With beta on (f_m - f_i) the nonlinear weights ignore a constant shift of the data, so
+    q(f + c) - q(f) = c sum_m omega_m sum_j w_mj is exactly linear in c; with the zero-mean beta
+    of the paper it is not.  Constant data give beta = 0, omega = gamma / sum(gamma); next to a
+    jump the flat sub-stencil has beta = 0 exactly and takes all the weight."""
+    o = _oracle_1d(R, 12.0, beta_mean=True)
+    oz = _oracle_1d(R, 12.0)
+    t = o.tables
+    rng = np.random.default_rng(3 + R)
+    f = rng.normal(size=2 * R + 1)
+    d1 = o.gp_weno(f + 0.7) - o.gp_weno(f)
+    d2 = o.gp_weno(f + 1.4) - o.gp_weno(f)
+    assert abs(d2 - 2.0 * d1) < 1e-12
+    z1 = oz.gp_weno(f + 0.7) - oz.gp_weno(f)
+    z2 = oz.gp_weno(f + 1.4) - oz.gp_weno(f)
+    assert abs(z2 - 2.0 * z1) > 1e-6
+    s_m = np.array([t["wl"][m].sum() for m in range(R + 1)])
+    qc = o.gp_weno(np.full(2 * R + 1, 2.0))
+    assert abs(qc - 2.0 * (t["gl"] * s_m).sum() / t["gl"].sum()) < 1e-14
+    g = np.ones(2 * R + 1)
+    g[R + 1:] = 2.0
+    assert abs(o.gp_weno(g) - s_m[0]) < 1e-12
+
+
+def test_poly_candidates_are_lagrange():
+    """The hybrid's candidate weights are Lagrange interpolation weights and its linear weights
+    the classical ones (1/16, 10/16, 5/16 for R=2): exact, not a limit."""
+    from fractions import Fraction
+    from oracle import gp_tables
+    t = gp_tables.tables(2, 12.0, 3.0, 0.5, poly=True)
+    np.testing.assert_allclose(t["gamma"], [1 / 16, 10 / 16, 5 / 16], rtol=1e-15)
+    np.testing.assert_allclose(t["w_sub"][0], [3 / 8, -5 / 4, 15 / 8], rtol=1e-15)
+    np.testing.assert_allclose(t["w_big"], [3 / 128, -5 / 32, 45 / 64, 15 / 32, -5 / 128], rtol=1e-15)
+    res = t["M"] @ t["gamma"] - t["w_big"]
+    assert np.abs(res).max() < 1e-15
+
+
+def test_poly_hybrid_convergence():
+    """Polynomial candidates with GP smoothness indicators keep the (2R+1)th order on smooth
+    advection (R=2: 4.5 between 100 and 200 cells; the GP candidates give 4.8 there)."""
+    errs = []
+    for n in (100, 200):
+        Ug, m = W.gaussian_1d(n)
+        oo = oracle.Oracle((n,), m["dx"], m["bc"], R=2, ell_over_dx=0.1 * n, gamma=m["gamma"], candidates="poly")
+        dx = m["dx"][0]
+        dt = 0.4 * dx / 2.3 * (dx / (1.0 / 25)) ** (5 / 3.0 - 1.0)
+        steps = int(math.ceil(1.0 / dt))
+        Un = oo.run(Ug, 1.0 / steps, steps)
+        Ue, _ = W.gaussian_1d(n, t=1.0)
+        errs.append(np.abs(Un[0] - Ue[0]).mean())
+    order = math.log(errs[0] / errs[1], 2)
+    assert order > 4.2, (errs, order)
+
+
+def test_nonzero_mean_removes_square_wave_overshoot():
+    """Section 7.1's scalar-advection discussion: with the zero mean the GP smoothness
+    indicators favour data near zero, so a flat square wave overshoots at its edges;
+    beta on f - f_centre removes the overshoot and is more diffusive (larger L1).
+    Density square wave (1 and 2) advected once around a periodic 200-cell domain at
+    u = p = 1, R = 2, l/dx = 12, CFL 0.4."""
+    n = 200
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where((x > 0.25) & (x < 0.75), 2.0, 1.0)
+    U0 = W.conserved(rho, [np.ones(n)], np.ones(n), 1.4)
+    res = {}
+    for mean in (False, True):
+        o = oracle.Oracle((n,), (1.0 / n,), (("periodic", "periodic"),), R=2, ell_over_dx=12.0, beta_mean=mean)
+        dt = 0.4 / o.max_rate(U0)
+        steps = int(math.ceil(1.0 / dt))
+        r = o.run(U0, 1.0 / steps, steps)[0]
+        res[mean] = (r.max() - 2.0, 1.0 - r.min(), np.abs(r - rho).mean())
+    assert res[False][0] > 0.02                        # several percent of the jump
+    assert res[True][0] < 1e-3 and res[True][1] < 1e-3
+    assert res[True][2] > res[False][2]                # the price: more diffusion
