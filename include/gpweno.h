@@ -77,7 +77,15 @@ typedef struct {
  *   flux_form      face flux of Eq. riemann_prob on the GP-WENO states:
  *                  0 = local Lax-Friedrichs (default), 1 = HLLC with Einfeldt
  *                  wave speeds from the Roe average (the paper's default
- *                  solver, Section 7). */
+ *                  solver, Section 7).
+ *   beta_mean      0 = zero-mean GP smoothness indicators, beta on f_m (the
+ *                  paper's choice, Eq. gp-smooth); 1 = non-zero mean, beta on
+ *                  f_m - f_i with f_i the centre value of the stencil (the
+ *                  variant of Sections 3.3 and 7.1).
+ *   candidates     0 = GP candidate predictions (Eq. candidate_interp);
+ *                  1 = polynomial (Lagrange) candidates and their linear
+ *                  weights with the GP smoothness indicators (the paper's
+ *                  WENO-GP hybrid). */
 typedef struct {
     double sigma_over_dx;
     double eps;
@@ -85,6 +93,8 @@ typedef struct {
     int dtype;
     double cfl;
     int flux_form;
+    int beta_mean;
+    int candidates;
 } gpweno_opts;
 
 void gpweno_default_opts(gpweno_opts *opts);
@@ -117,12 +127,12 @@ gpweno_status gpweno_plan_tables(gpweno_plan plan, double *w_m, double *gam, dou
 
 /* Host-only: the double-double GP tables of gpweno_plan_create without a
  * plan or a device (for checking the precompute on machines without a GPU).
- * Left-state tables as in gpweno_plan_tables; w_m_r, gam_r are the tables
+ * `candidates` as in gpweno_opts.  Left-state tables as in gpweno_plan_tables; w_m_r, gam_r are the tables
  * of the right state of face i+1/2 (x* = x_{i+1} - dx/2, stencil of cell
  * i+1).  Any output pointer may be NULL.  Returns GPWENO_ERR_ARG or
  * GPWENO_ERR_PRECOMPUTE as gpweno_plan_create would. */
-gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_m, double *gam, double *P,
-                               double *w_big, double *w_m_r, double *gam_r);
+gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, double *w_m,
+                               double *gam, double *P, double *w_big, double *w_m_r, double *gam_r);
 
 /* dUdt = L(U): the right-hand side of Eq. disc_fd with the corrected fluxes
  * of Eq. numFlux_cor.  U, dUdt: device state arrays (see conventions);
@@ -172,11 +182,11 @@ gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *d
  * p <= 0 or a NaN; returns GPWENO_ERR_CUDA if an earlier launch failed. */
 gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 
-/* Batched 2D stepping (the task's batching pattern; same per-face scheme as
- * gpweno_rk3_step): one persistent launch per RK stage serves n independent 2D
- * plans of possibly different grid size, R, l/dx, sigma and boundary
- * conditions (all plans must share dtype and device; at most 12 distinct
- * (l/dx, sigma, gamma, eps, p) sets per radius).  The host cuts every
+/* Batched 2D stepping (same per-face scheme as gpweno_rk3_step): one
+ * persistent launch per RK stage serves n independent 2D plans of possibly
+ * different grid size, R, l/dx, sigma, face flux, candidates and boundary
+ * conditions (all plans must share dtype and device and use beta_mean = 0,
+ * else GPWENO_ERR_ARG; at most 12 distinct table sets per radius).  The host cuts every
  * instance into strips and row segments and hands each CTA a contiguous run of
  * segments of equal estimated cost.  The batch refers to the member plans,
  * which must outlive it.  tune_cache: NULL, or the path of a text file of

@@ -62,6 +62,8 @@ void gpweno_default_opts(gpweno_opts *o)
     o->dtype = GPWENO_F64;
     o->cfl = 0.0;
     o->flux_form = 0;
+    o->beta_mean = 0;
+    o->candidates = 0;
 }
 
 const char *gpweno_last_error(void) { return g_err; }
@@ -97,6 +99,10 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     }
     if (!(o.eps > 0.0) || (o.dtype == GPWENO_F32 && o.eps < 1.2e-38)) {
         set_error("eps=%g must be positive (and a normal FP32 number for dtype F32)", o.eps);
+        return GPWENO_ERR_ARG;
+    }
+    if ((o.beta_mean != 0 && o.beta_mean != 1) || (o.candidates != 0 && o.candidates != 1)) {
+        set_error("beta_mean=%d and candidates=%d must each be 0 or 1", o.beta_mean, o.candidates);
         return GPWENO_ERR_ARG;
     }
     if (o.flux_form != 0 && o.flux_form != 1) {
@@ -145,7 +151,7 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     p->opts = o;
     p->ncell = ncell;
     char err[256];
-    int rc = gp_precompute(R, ell_over_dx, o.sigma_over_dx, &p->tab, err, sizeof(err));
+    int rc = gp_precompute(R, ell_over_dx, o.sigma_over_dx, &p->tab, err, sizeof(err), o.candidates);
     if (rc) {
         set_error("%s", err);
         delete p;
@@ -190,12 +196,16 @@ gpweno_status gpweno_plan_tables(gpweno_plan p, double *w_m, double *gam, double
     return GPWENO_OK;
 }
 
-gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_m, double *gam, double *P,
-                               double *w_big, double *w_m_r, double *gam_r)
+gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, double *w_m,
+                               double *gam, double *P, double *w_big, double *w_m_r, double *gam_r)
 {
     GpTables t;
     char err[256];
-    int rc = gp_precompute(R, ell_over_dx, sigma_over_dx, &t, err, sizeof(err));
+    if (candidates != 0 && candidates != 1) {
+        set_error("candidates=%d must be 0 or 1", candidates);
+        return GPWENO_ERR_ARG;
+    }
+    int rc = gp_precompute(R, ell_over_dx, sigma_over_dx, &t, err, sizeof(err), candidates);
     if (rc) {
         set_error("%s", err);
         return rc == 1 ? GPWENO_ERR_ARG : GPWENO_ERR_PRECOMPUTE;
@@ -354,6 +364,10 @@ gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int 
         gpweno_plan p = plans[k];
         if (!p || p->is_batch || p->dims.ndim != 2) {
             set_error("gpweno_plan_batch: plan %d is not a 2D single-grid plan", k);
+            return GPWENO_ERR_ARG;
+        }
+        if (p->opts.beta_mean) {
+            set_error("gpweno_plan_batch: plan %d uses beta_mean = 1, which batches do not support", k);
             return GPWENO_ERR_ARG;
         }
         if (p->opts.dtype != plans[0]->opts.dtype || p->device != plans[0]->device) {

@@ -126,7 +126,7 @@ gpweno_status build_batch_T(gpweno_plan b)
         for (int q = 0; q < (int)rv.size(); ++q)
             if (rv[q]->ell == p->ell && rv[q]->opts.sigma_over_dx == p->opts.sigma_over_dx &&
                 rv[q]->gamma == p->gamma && rv[q]->opts.eps == p->opts.eps && rv[q]->opts.p == p->opts.p &&
-                rv[q]->opts.flux_form == p->opts.flux_form)
+                rv[q]->opts.flux_form == p->opts.flux_form && rv[q]->opts.candidates == p->opts.candidates)
                 idx = q;
         if (idx < 0) {
             if ((int)rv.size() >= kBatchMaxSets) {

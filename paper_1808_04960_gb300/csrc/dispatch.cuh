@@ -69,7 +69,9 @@ StageArgs<T> base_args(const gpweno_plan_s *p)
     return a;
 }
 
-template <typename T, int R>
+// MEAN: the non-zero-mean smoothness indicators (beta on f - f_centre), a
+// compile-time switch so that the default kernels keep their register budget.
+template <typename T, int R, bool MEAN>
 gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t st)
 {
     StageArgs<T> a = a0;
@@ -79,7 +81,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         // (1) xy-plane kernel: P = -(div_x/dx + div_y/dy)
         {
             const size_t smem = stage2d_smem_bytes<T, R, NT, 5>();
-            auto kern = plane3d_kernel<T, R, NT>;
+            auto kern = plane3d_kernel<T, R, NT, MEAN>;
             static int occ = 0;
             if (!occ) {
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -105,7 +107,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         // (2) z-marching kernel: L = P - div_z/dz and the stage update
         {
             const size_t smem = stagez_smem_bytes<T, R, NT>();
-            auto kern = stagez_kernel<T, R, NT>;
+            auto kern = stagez_kernel<T, R, NT, MEAN>;
             static int occ = 0;
             if (!occ) {
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -121,7 +123,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     } else if (p->dims.ndim == 2) {
         constexpr int NT = kNT2D;
         const size_t smem = stage2d_smem_bytes<T, R, NT>();
-        auto kern = stage2d_kernel<T, R, NT>;
+        auto kern = stage2d_kernel<T, R, NT, MEAN>;
         static int occ = 0;   // per instantiation: resident CTAs per SM
         if (!occ) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -140,7 +142,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     } else {
         constexpr int NT = kNT1D;
         const size_t smem = stage1d_smem_bytes<T, R, NT>();
-        auto kern = stage1d_kernel<T, R, NT>;
+        auto kern = stage1d_kernel<T, R, NT, MEAN>;
         a.nstrips = (a.n[0] + (NT - 5) - 1) / (NT - 5);
         a.W = (a.n[0] + a.nstrips - 1) / a.nstrips;
         a.H = 1;
@@ -153,7 +155,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     return GPWENO_OK;
 }
 
-template <typename T>
+template <typename T, bool MEAN>
 gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
     StageArgs<T> a = base_args<T>(p);
@@ -172,9 +174,9 @@ gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
     a.dt_dev = io.dt_dev;
     a.rate = io.want_rate ? p->ws : nullptr;
     switch (p->R) {
-    case 1: return launch_stage_R<T, 1>(p, a, st);
-    case 2: return launch_stage_R<T, 2>(p, a, st);
-    case 3: return launch_stage_R<T, 3>(p, a, st);
+    case 1: return launch_stage_R<T, 1, MEAN>(p, a, st);
+    case 2: return launch_stage_R<T, 2, MEAN>(p, a, st);
+    case 3: return launch_stage_R<T, 3, MEAN>(p, a, st);
     default: set_error("R=%d not compiled", p->R); return GPWENO_ERR_ARG;
     }
 }

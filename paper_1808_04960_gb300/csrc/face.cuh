@@ -169,7 +169,7 @@ __device__ __forceinline__ bool prim_pert(const PrimRef<T, NC> &r, const T (&w)[
 //     V_{s+1} + R (q_R - L V_{s+1}), using R L = I and sum_m omega_m = 1;
 //   * fluxes and conserved states are perturbations about V_s (prim_pert).
 // Returns false on a non-physical Roe, left, right or neighbour state.
-template <typename T, int NC, int R>
+template <typename T, int NC, int R, bool MEAN = false>
 __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
                                          T (&B)[NC])
 {
@@ -263,16 +263,11 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
 #pragma unroll
         for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : lrow(kk, dV[j]);
 
-        // --- smoothness indicators on the R+2 windows d[w..w+R] --------
-        // P_h . f_w = P_h . d_w + f_c sum_j P_hj for the symmetric rows; the
-        // f_c term is the same for every window.
-        T pf[S];
-#pragma unroll
-        for (int h = 0; h < S; ++h) pf[h] = (h % 2 == 0) ? tb.Psum[h] * fc : T(0);
-        // xw_w = (eps + beta_w)^-p, shared by the two sides of the face
-        T xw[R + 2];
-#pragma unroll
-        for (int w = 0; w < R + 2; ++w) {
+        // --- smoothness indicators ------------------------------------------
+        // beta over window d[w..w+R] with the data shifted by a constant c (P_h . (f - c) =
+        // P_h . d + (f_c - c) sum_j P_hj; only the symmetric rows have a non-zero sum):
+        // returns (eps + beta)^-p
+        auto beta_x = [&](int w, const T (&pf)[S]) -> T {
             T ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
 #pragma unroll
             for (int j = 0; j < HALF; ++j) {
@@ -297,25 +292,38 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
                 beta = fma(dot, dot, beta);
             }
             const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(tb.eps, beta), Num<T>::eps_floor()));
-            xw[w] = tb.p == 2 ? Num<T>::mul_rn(x, x) : x;   // (eps + beta)^-p
+            return tb.p == 2 ? Num<T>::mul_rn(x, x) : x;
+        };
+        // zero mean: both sides shift by f_c, so the right side's window m is the
+        // left side's window m+1 and the R+2 windows are shared.  Mean f_centre:
+        // the left side's centre is cell s (no shift), the right side's is cell
+        // s+1 (shift by d_{R+1}), and the 2R+2 windows are separate.
+        T pfl[S], pfr[S];
+#pragma unroll
+        for (int h = 0; h < S; ++h) {
+            pfl[h] = (h % 2 == 0 && !MEAN) ? tb.Psum[h] * fc : T(0);
+            pfr[h] = (h % 2 == 0) ? (MEAN ? -tb.Psum[h] * d[R + 1] : pfl[h]) : T(0);
         }
         // --- candidates relative to the centre cells and nonlinear weights ---
         // omega_m ~ gamma_m (eps + beta_m)^-p  (Eq. weights); sum_m omega_m = 1 is used exactly.
         T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
+        T xl = beta_x(0, pfl);
 #pragma unroll
         for (int m = 0; m <= R; ++m) {
+            const T xr = beta_x(m + 1, pfr);
             T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
 #pragma unroll
             for (int j = 0; j <= R; ++j) {
                 if (m + j != R) sl = fma(tb.wl[m][j], d[m + j], sl);
                 if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
             }
-            const T yl = Num<T>::mul_rn(tb.gl[m], xw[m]);
-            const T yr = Num<T>::mul_rn(tb.gr[m], xw[m + 1]);
+            const T yl = Num<T>::mul_rn(tb.gl[m], xl);
+            const T yr = Num<T>::mul_rn(tb.gr[m], xr);
             numL = fma(yl, sl, numL);
             denL = Num<T>::add_rn(denL, yl);
             numR = fma(yr, sr, numR);
             denR = Num<T>::add_rn(denR, yr);
+            if (m < R) xl = MEAN ? beta_x(m + 1, pfl) : xr;
         }
         dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
         dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}

@@ -197,10 +197,27 @@ void chol_solve(const Chol &ch, const dd *b, dd *x)
     }
 }
 
-// GP weights for the points 2*p2[k] (half-units) and the prediction point xs2
-// (half-units): w = K^{-1} k*.
-bool gp_weights(dd q, const int *pts2, int n, int xs2, dd *w, double *cond)
+// Lagrange interpolation weights at xs2 for the points pts2 (half-units):
+// l_j = prod_{k != j} (xs2 - p_k) / (p_j - p_k), ratios of small integers.
+void lagrange_weights(const int *pts2, int n, int xs2, dd *w)
 {
+    for (int j = 0; j < n; ++j) {
+        dd v = make(1.0);
+        for (int k = 0; k < n; ++k)
+            if (k != j) v = div(mul_d(v, (double)(xs2 - pts2[k])), make((double)(pts2[j] - pts2[k])));
+        w[j] = v;
+    }
+}
+
+// GP weights for the points 2*p2[k] (half-units) and the prediction point xs2
+// (half-units): w = K^{-1} k*; with `poly`, Lagrange weights instead.
+bool gp_weights(dd q, const int *pts2, int n, int xs2, dd *w, double *cond, int poly = 0)
+{
+    if (poly) {
+        lagrange_weights(pts2, n, xs2, w);
+        if (cond) *cond = 1.0;
+        return true;
+    }
     dd K[kMaxBig][kMaxBig];
     dd ks[kMaxBig];
     for (int a = 0; a < n; ++a) {
@@ -259,13 +276,13 @@ void jacobi(dd A[kMaxS][kMaxS], int n, dd V[kMaxS][kMaxS])
 // Linear weights for one prediction point: sub-stencil weights, full-stencil
 // weights, then least squares of M gamma = w through the normal equations.
 bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam, double *resid, double *cond,
-                 double *sum1, char *err, std::size_t errlen)
+                 double *sum1, char *err, std::size_t errlen, int poly)
 {
     const int S = R + 1, B = 2 * R + 1;
     int big2[kMaxBig];
     for (int j = 0; j < B; ++j) big2[j] = 2 * (j - R);
     dd wb[kMaxBig];
-    if (!gp_weights(q, big2, B, xs2, wb, cond)) {
+    if (!gp_weights(q, big2, B, xs2, wb, cond, poly)) {
         std::snprintf(err, errlen, "covariance K of the %d-point stencil is not positive definite in double-double", B);
         return false;
     }
@@ -273,7 +290,7 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
     for (int m = 0; m < S; ++m) {
         int p2[kMaxS];
         for (int j = 0; j < S; ++j) p2[j] = 2 * (-R + m + j);
-        if (!gp_weights(q, p2, S, xs2, ws[m], nullptr)) {
+        if (!gp_weights(q, p2, S, xs2, ws[m], nullptr, poly)) {
             std::snprintf(err, errlen, "sub-stencil covariance K_m is not positive definite in double-double");
             return false;
         }
@@ -322,7 +339,7 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
 
 }  // namespace
 
-int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std::size_t errlen)
+int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std::size_t errlen, int poly)
 {
     if (R < 1 || R > kMaxR) {
         std::snprintf(err, errlen, "R=%d out of range [1,%d]", R, kMaxR);
@@ -343,9 +360,10 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
     dd ql = exp_dd(neg(div(make(1.0), mul_d(mul(make(ell), make(ell)), 8.0))));
     dd qs = exp_dd(neg(div(make(1.0), mul_d(mul(make(sigma), make(sigma)), 8.0))));
     double cond = 0.0, resid_r = 0.0;
-    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, out->sl1, err, errlen))
+    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, out->sl1, err, errlen, poly))
         return 2;
-    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen)) return 2;
+    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen, poly))
+        return 2;
     out->cond_estimate = cond;
     // double-double carries ~2^-104 relative; demand cond * 2^-104 < 1e-6
     if (cond * 4.93e-32 > 1e-6) {

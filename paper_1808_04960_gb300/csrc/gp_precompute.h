@@ -37,6 +37,10 @@ struct GpTables {
 
 // Returns 0 on success; otherwise writes a message to err and returns
 // 1 (bad argument) or 2 (ill-conditioned beyond double-double).
-int gp_precompute(int R, double ell_over_dx, double sigma_over_dx, GpTables *out, char *err, std::size_t errlen);
+// poly = 1: candidate and full-stencil weights are Lagrange (polynomial)
+// interpolation weights instead of GP weights (the WENO-GP hybrid); the linear
+// weights, K_m(sigma) and P are computed as usual.
+int gp_precompute(int R, double ell_over_dx, double sigma_over_dx, GpTables *out, char *err, std::size_t errlen,
+                  int poly = 0);
 
 }  // namespace gpweno

@@ -8,7 +8,8 @@ namespace gpweno {
 
 gpweno_status launch_stage_f32(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    return launch_stage_T<float>(p, io, st);
+    if (p->opts.beta_mean) return launch_stage_f32_mean(p, io, st);
+    return launch_stage_T<float, false>(p, io, st);
 }
 
 gpweno_status launch_max_rate_f32(gpweno_plan p, const void *U, cudaStream_t st)

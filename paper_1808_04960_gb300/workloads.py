@@ -17,6 +17,7 @@ Problems (shapes and distributions of the paper's test problems):
   isentropic_vortex    Shu's isentropic vortex, Section 6.2 (periodic square)
   four_quadrant        2D four-state Riemann problem with seeded states (Section 7.5 family)
   shock_turbulence_3d  Mach-3 shock into a seeded multi-mode density field
+  smooth_field         seeded smooth periodic field, every primitive varying at O(amp)
   batch_instances      list of seeded 2D instances of uneven size, R and l/Delta
 """
 from __future__ import annotations
@@ -160,6 +161,31 @@ def shock_turbulence_3d(n=64, seed=4, gamma=1.4, mach=3.0, nmodes=32, kmax=8, rm
     return U, dict(dx=(dx, dx, dx),
                    bc=(("outflow", "outflow"), ("periodic", "periodic"), ("periodic", "periodic")),
                    gamma=gamma, cfl=0.4, post=(rho2, u2, p2))
+
+
+def smooth_field(shape, seed=0, amp=0.2, nmodes=3, gamma=1.4):
+    """Seeded smooth periodic field on the unit box: each primitive (rho, u..., p)
+    is a base value plus `nmodes` random Fourier modes (wave numbers 1..3 per
+    axis, amplitude amp/nmodes each), so that no characteristic field is constant.
+    ``shape`` is the grid in array order ((nx,), (ny, nx) or (nz, ny, nx))."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    rng = np.random.default_rng(seed)
+    axes = [_centres(n, 0.0, 1.0) for n in reversed(shape)]      # x, y, z
+    grids = np.meshgrid(*[a[0] for a in reversed(axes)], indexing="ij")[::-1]   # X, Y, Z in array shape
+    base = [1.0] + [0.3] * nd + [1.0]
+    prims = []
+    for b in base:
+        f = np.full(shape, b)
+        for _ in range(nmodes):
+            k = rng.integers(1, 4, nd)
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            arg = sum(2.0 * math.pi * k[d] * grids[d] for d in range(nd)) + ph
+            f = f + (amp / nmodes) * np.sin(arg)
+        prims.append(f)
+    U = conserved(prims[0], prims[1:1 + nd], prims[-1], gamma)
+    dx = tuple(a[1] for a in axes)
+    return U, dict(dx=dx, bc=(("periodic", "periodic"),) * nd, gamma=gamma)
 
 
 def batch_instances(count=256, seed=5, nmin=64, nmax=1024, gamma=1.4):

@@ -80,3 +80,43 @@ def test_plan_argument_checks_before_device(lib):
 def test_batch_needs_plans(lib):
     with pytest.raises(gpweno.GpwenoError):
         gpweno.BatchPlan([])
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_dd_poly_tables_match_oracle(lib, R):
+    """Polynomial (Lagrange) candidates: the library's tables agree with the oracle's
+    100-digit ones, and at R = 2 the linear weights are the classical 1/16, 10/16, 5/16."""
+    t = gpweno.gp_tables(R, 12.0, 3.0, candidates="poly")
+    ol = OT.tables(R, 12.0, 3.0, 0.5, poly=True)
+    orr = OT.tables(R, 12.0, 3.0, -0.5, poly=True)
+    np.testing.assert_allclose(t["w_sub"], ol["w_sub"], rtol=0, atol=1e-14 * np.abs(ol["w_sub"]).max())
+    np.testing.assert_allclose(t["w_big"], ol["w_big"], rtol=0, atol=1e-14 * np.abs(ol["w_big"]).max())
+    np.testing.assert_allclose(t["gamma"], ol["gamma"], rtol=1e-14, atol=0)
+    np.testing.assert_allclose(t["w_sub_r"], orr["w_sub"], rtol=0, atol=1e-14 * np.abs(orr["w_sub"]).max())
+    np.testing.assert_allclose(t["gamma_r"], orr["gamma"], rtol=1e-14, atol=0)
+    if R == 2:
+        np.testing.assert_allclose(t["gamma"], [1 / 16, 10 / 16, 5 / 16], rtol=1e-15)
+    # the smoothness-indicator tables do not depend on the candidates
+    g = gpweno.gp_tables(R, 12.0, 3.0)
+    np.testing.assert_array_equal(t["P"], g["P"])
+
+
+def test_variant_options_checked(lib):
+    """beta_mean and candidates outside {0, 1} are refused by the C ABI before any device work."""
+    import ctypes
+    with pytest.raises(gpweno.GpwenoError) as e:
+        gpweno._check(lib.gpweno_gp_tables(2, 12.0, 3.0, 2, None, None, None, None, None, None), "gp_tables")
+    assert e.value.status == gpweno.ERR_ARG
+    dims = gpweno.Dims()
+    dims.ndim = 2
+    for a in range(3):
+        dims.n[a] = 16 if a < 2 else 1
+        dims.dx[a] = 0.1
+        dims.bc_lo[a] = dims.bc_hi[a] = 0
+    for field in ("beta_mean", "candidates"):
+        o = gpweno.Opts()
+        lib.gpweno_default_opts(ctypes.byref(o))
+        setattr(o, field, 3)
+        h = ctypes.c_void_p()
+        st = lib.gpweno_plan_create(ctypes.byref(h), 2, 12.0, ctypes.byref(dims), 1.4, ctypes.byref(o))
+        assert st == gpweno.ERR_ARG and not h.value, field
