@@ -79,6 +79,8 @@ def _load():
             lib.oracle_gp_weno.restype = ctypes.c_double
             lib.oracle_hllc.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double, ctypes.c_double, dp]
             lib.oracle_hllc.restype = None
+            lib.oracle_hll.argtypes = lib.oracle_hllc.argtypes
+            lib.oracle_hll.restype = None
             lib.oracle_corrected_flux.argtypes = [dp]
             lib.oracle_corrected_flux.restype = ctypes.c_double
             _lib = lib
@@ -122,7 +124,7 @@ class Oracle:
         c.eps = float(eps)
         c.p = int(p)
         c.wl, c.gl, c.wr, c.gr, c.Kinv = [a.ctypes.data for a in self._keep]
-        c.flux = {"lf": 0, "hllc": 1}[flux]
+        c.flux = {"lf": 0, "hllc": 1, "hll": 2}[flux]
         c.beta_mean = 1 if beta_mean else 0
         self.cfg = c
         self.R = int(R)
@@ -201,6 +203,16 @@ def hllc(uL, uR, uroe, croe, gamma=1.4):
     uR = np.ascontiguousarray(uR, dtype=np.float64)
     F = np.zeros(uL.shape[0])
     lib.oracle_hllc(uL.shape[0], float(gamma), _ptr(uL), _ptr(uR), float(uroe), float(croe), _ptr(F))
+    return F
+
+
+def hll(uL, uR, uroe, croe, gamma=1.4):
+    """HLL flux of two conserved normal-first states (Einfeldt speeds from the given Roe values)."""
+    lib = _load()
+    uL = np.ascontiguousarray(uL, dtype=np.float64)
+    uR = np.ascontiguousarray(uR, dtype=np.float64)
+    F = np.zeros(uL.shape[0])
+    lib.oracle_hll(uL.shape[0], float(gamma), _ptr(uL), _ptr(uR), float(uroe), float(croe), _ptr(F))
     return F
 
 

@@ -59,7 +59,7 @@ typedef struct {
     const double *wr;  /* [(R+1)][(R+1)] sub-stencil weights, prediction at x* = -1/2 */
     const double *gr;  /* [(R+1)] linear weights at x* = -1/2 */
     const double *Kinv;/* [(R+1)][(R+1)] inverse of K_m built with sigma */
-    int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC */
+    int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC, 2 = HLL */
     int beta_mean;     /* 0 = zero-mean GP smoothness indicators (the paper's choice), 1 = mean f_centre */
 } oracle_cfg;
 
@@ -238,6 +238,27 @@ static void hllc_flux(const double *uL, const double *uR, int nc, double g, doub
     for (int a = 0; a < nc; ++a) F[a] = fK[a] + SK * (us[a] - uK[a]);
 }
 
+/* HLL flux (Harten, Lax and van Leer's two-wave solver) of two conserved
+ * normal-first states with the same Einfeldt speeds as hllc_flux:
+ * F = F_L if S_L >= 0, F_R if S_R <= 0, else
+ * (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L). */
+static void hll_flux(const double *uL, const double *uR, int nc, double g, double uroe, double croe, double *F)
+{
+    double rL = uL[0], rR = uR[0];
+    double vL = uL[1] / rL, vR = uR[1] / rR;
+    double pL = pressure(uL, nc, g), pR = pressure(uR, nc, g);
+    double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    double SL = fmin(vL - cL, uroe - croe), SR = fmax(vR + cR, uroe + croe);
+    double fL[OR_MAXC], fR[OR_MAXC];
+    normal_flux(uL, nc, g, fL);
+    normal_flux(uR, nc, g, fR);
+    for (int a = 0; a < nc; ++a) {
+        if (SL >= 0.0) F[a] = fL[a];
+        else if (SR <= 0.0) F[a] = fR[a];
+        else F[a] = (SR * fL[a] - SL * fR[a] + SL * SR * (uR[a] - uL[a])) / (SR - SL);
+    }
+}
+
 /* Face flux F between cells s and s+1 along dimension d, at transverse
  * position (t1, t2) meaning the other two cell indices in natural order.
  * Writes nc values (natural component order).  Returns 0 on a non-physical
@@ -296,6 +317,8 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
     double Fn[OR_MAXC];
     if (c->flux == 1) {
         hllc_flux(uL, uR, nc, c->gamma, roe[1], roe[nc], Fn);
+    } else if (c->flux == 2) {
+        hll_flux(uL, uR, nc, c->gamma, roe[1], roe[nc], Fn);
     } else {
         double cL = sqrt(c->gamma * pL / uL[0]), cR = sqrt(c->gamma * pR / uR[0]);
         double aL = fabs(uL[1] / uL[0]) + cL, aR = fabs(uR[1] / uR[0]) + cR;
@@ -413,6 +436,12 @@ double oracle_max_rate(const oracle_cfg *c, const double *U)
 void oracle_hllc(int nc, double g, const double *uL, const double *uR, double uroe, double croe, double *F)
 {
     hllc_flux(uL, uR, nc, g, uroe, croe, F);
+}
+
+/* HLL flux, exposed for unit tests (arguments as oracle_hllc). */
+void oracle_hll(int nc, double g, const double *uL, const double *uR, double uroe, double croe, double *F)
+{
+    hll_flux(uL, uR, nc, g, uroe, croe, F);
 }
 
 /* Single face, exposed for unit tests: Riemann states and flux at the face

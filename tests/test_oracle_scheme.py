@@ -371,6 +371,90 @@ def test_hllc_scheme_free_stream_and_order():
 
 
 # ---------------------------------------------------------------------------
+# HLL face flux (the solver of the paper's Mach-3 wind-tunnel test, Section 7)
+
+def _einfeldt(uL, uR, g=1.4):
+    ur, cr = _roe_uc(uL, uR, g)
+    rL, rR = uL[0], uR[0]
+    vL, vR = uL[1] / rL, uR[1] / rR
+    pL = (g - 1) * (uL[-1] - 0.5 * np.sum(uL[1:-1] ** 2) / rL)
+    pR = (g - 1) * (uR[-1] - 0.5 * np.sum(uR[1:-1] ** 2) / rR)
+    SL = min(vL - math.sqrt(g * pL / rL), ur - cr)
+    SR = max(vR + math.sqrt(g * pR / rR), ur + cr)
+    return ur, cr, SL, SR
+
+
+@pytest.mark.parametrize("nc", [3, 4, 5])
+def test_hll_is_the_integral_average_flux(nc):
+    """Toro's derivation of HLL: with the intermediate state U* = (S_R U_R - S_L U_L - (F_R - F_L)) /
+    (S_R - S_L) (conservation over the wave fan), F_HLL = F_L + S_L (U* - U_L) = F_R + S_R (U* - U_R);
+    F(U, U) = F(U); supersonic states take the upwind flux."""
+    g = 1.4
+    rng = np.random.default_rng(70 + nc)
+    for _ in range(10):
+        uL, uR = rand_state(rng, nc), rand_state(rng, nc)
+        ur, cr, SL, SR = _einfeldt(uL, uR)
+        F = oracle.hll(uL, uR, ur, cr)
+        fL, fR = euler_flux(uL, g), euler_flux(uR, g)
+        if SL < 0 < SR:
+            Us = (SR * uR - SL * uL - (fR - fL)) / (SR - SL)
+            np.testing.assert_allclose(F, fL + SL * (Us - uL), rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(F, fR + SR * (Us - uR), rtol=1e-12, atol=1e-12)
+        u = rand_state(rng, nc)
+        ur, cr = _roe_uc(u, u)
+        np.testing.assert_allclose(oracle.hll(u, u, ur, cr), euler_flux(u, g), rtol=1e-13, atol=1e-13)
+    uL = W.conserved(np.array(1.0), [np.array(-3.0)] + [np.array(0.1)] * (nc - 3), np.array(1.0), g)
+    uR = W.conserved(np.array(0.8), [np.array(-2.9)] + [np.array(-0.2)] * (nc - 3), np.array(0.9), g)
+    ur, cr = _roe_uc(uL, uR)
+    np.testing.assert_allclose(oracle.hll(uL, uR, ur, cr), euler_flux(uR, g), rtol=1e-13)
+
+
+def test_hll_smears_a_stationary_contact():
+    """A stationary contact (u = 0, equal p): HLLC's mass flux is zero, HLL's is the textbook
+    diffusive S_L S_R (rho_R - rho_L) / (S_R - S_L) != 0."""
+    g = 1.4
+    uL = W.conserved(np.array(1.0), [np.array(0.0), np.array(0.0)], np.array(1.0), g)
+    uR = W.conserved(np.array(0.2), [np.array(0.0), np.array(0.0)], np.array(1.0), g)
+    ur, cr, SL, SR = _einfeldt(uL, uR)
+    F = oracle.hll(uL, uR, ur, cr)
+    assert abs(oracle.hllc(uL, uR, ur, cr)[0]) < 1e-15
+    np.testing.assert_allclose(F[0], SL * SR * (uR[0] - uL[0]) / (SR - SL), rtol=1e-13)
+    assert abs(F[0]) > 0.1
+
+
+def test_hll_scheme_free_stream_mirror_and_order():
+    """The whole scheme with HLL: free streams exactly, mirror symmetry, and the Table 1 order."""
+    rng = np.random.default_rng(3)
+    u0 = rand_state(rng, 4)
+    U = np.empty((4, 11, 13))
+    for a in range(4):
+        U[a] = u0[a]
+    o = oracle.Oracle((11, 13), (0.1, 0.1), (("outflow", "outflow"),) * 2, R=2, flux="hll")
+    assert np.abs(o.rhs(U)).max() == 0.0
+    U1, m = W.four_quadrant(24, seed=3, ny=20)
+    o = oracle.Oracle(U1.shape[1:], m["dx"], m["bc"], R=2, flux="hll")
+    Um = U1[:, :, ::-1].copy()
+    Um[1] = -Um[1]
+    r, rm = o.rhs(U1), o.rhs(Um)
+    rm = rm[:, :, ::-1]
+    rm[1] = -rm[1]
+    np.testing.assert_allclose(rm, r, rtol=0, atol=1e-12 * np.abs(r).max())
+    errs = []
+    for n in (50, 100):
+        Ug, m = W.gaussian_1d(n)
+        oo = oracle.Oracle((n,), m["dx"], m["bc"], R=2, ell_over_dx=0.1 * n, gamma=m["gamma"], flux="hll")
+        dx = m["dx"][0]
+        dt = 0.4 * dx / 2.3 * (dx / (1.0 / 25)) ** (5 / 3.0 - 1.0)
+        steps = int(math.ceil(1.0 / dt))
+        Un = oo.run(Ug, 1.0 / steps, steps)
+        Ue, _ = W.gaussian_1d(n, t=1.0)
+        errs.append(np.abs(Un[0] - Ue[0]).mean())
+    tab = _table1()
+    order = math.log(errs[0] / errs[1], 2)
+    assert abs(order - tab[100][4]) < 0.5, (errs, order)
+
+
+# ---------------------------------------------------------------------------
 # Variants: non-zero-mean smoothness indicators and the polynomial-candidate hybrid
 
 @pytest.mark.parametrize("R", [1, 2, 3])
