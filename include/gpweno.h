@@ -77,7 +77,8 @@ typedef struct {
  *   flux_form      face flux of Eq. riemann_prob on the GP-WENO states:
  *                  0 = local Lax-Friedrichs (default), 1 = HLLC with Einfeldt
  *                  wave speeds from the Roe average (the paper's default
- *                  solver, Section 7).
+ *                  solver, Section 7), 2 = HLL with the same speeds (the
+ *                  solver of the paper's Mach-3 wind-tunnel test, Section 7).
  *   beta_mean      0 = zero-mean GP smoothness indicators, beta on f_m (the
  *                  paper's choice, Eq. gp-smooth); 1 = non-zero mean, beta on
  *                  f_m - f_i with f_i the centre value of the stencil (the

@@ -105,8 +105,8 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
         set_error("beta_mean=%d and candidates=%d must each be 0 or 1", o.beta_mean, o.candidates);
         return GPWENO_ERR_ARG;
     }
-    if (o.flux_form != 0 && o.flux_form != 1) {
-        set_error("flux_form=%d: 0 (local Lax-Friedrichs) or 1 (HLLC)", o.flux_form);
+    if (o.flux_form < 0 || o.flux_form > 2) {
+        set_error("flux_form=%d: 0 (local Lax-Friedrichs), 1 (HLLC) or 2 (HLL)", o.flux_form);
         return GPWENO_ERR_ARG;
     }
     long ncell = 1;

@@ -96,7 +96,7 @@ struct FaceTables {
     T eps;                // WENO epsilon
     T gamma;              // ratio of specific heats
     int p;                // WENO power, 1 or 2
-    int flux;             // face flux: 0 local Lax-Friedrichs, 1 HLLC
+    int flux;             // face flux: 0 local Lax-Friedrichs, 1 HLLC, 2 HLL
 };
 
 // Primitive reference state of the "cell-relative" evaluation (normal-first order).
@@ -388,6 +388,20 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             else if (SR <= T(0)) f = GR[a];
             else if (Ss >= T(0)) f = fma(SL, dUL[a], GL[a]);
             else f = fma(SR, dUR[a], GR[a]);
+            A[a] = f;
+        }
+    } else if (tb.flux == 2) {
+        // HLL with the same Einfeldt speeds: F_L if S_L >= 0, F_R if S_R <= 0, else
+        // (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L); relative to F(U_s)
+        // the flux terms keep that form with G_K = F_K - F(U_s) and c_K = U_K - U_s.
+        const T SL = Num<T>::fmin(uL - aL, vel[0] - c), SR = Num<T>::fmax(uR + aR, vel[0] + c);
+        const T iS = Num<T>::rcp(SR - SL);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            T f;
+            if (SL >= T(0)) f = GL[a];
+            else if (SR <= T(0)) f = GR[a];
+            else f = (fma(SR, GL[a], -SL * GR[a]) + SL * SR * (cR[a] - cL[a])) * iS;
             A[a] = f;
         }
     } else {

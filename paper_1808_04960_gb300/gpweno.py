@@ -159,7 +159,7 @@ class Plan:
         opts.p = int(p)
         opts.dtype = F32 if dtype == "f32" else F64
         opts.cfl = float(cfl)
-        opts.flux_form = {"lf": 0, "hllc": 1}[flux]
+        opts.flux_form = {"lf": 0, "hllc": 1, "hll": 2}[flux]
         opts.beta_mean = 1 if beta_mean else 0
         opts.candidates = {"gp": 0, "poly": 1}[candidates]
         h = ctypes.c_void_p()
