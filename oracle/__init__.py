@@ -18,6 +18,12 @@ Parity status per function (pins are in ``tests/test_oracle_*.py``):
   corrected_flux            pinned (exact for degree-5 flux primitives)
   oracle_rhs / rk3          pinned (free-stream preservation, conservation,
                             mirror and rotation symmetry, smooth-vortex order)
+  FD-Flux (face_flux_fd)    pinned (reconstruction tables: closed-form covariances
+                            against quadrature, flat limit = WENO-JS reconstruction
+                            coefficients, exact polynomial reconstruction; scheme:
+                            free stream, conservation, mirror symmetry, order 2R+1
+                            with reconstruction weights and 2 with point weights,
+                            Eq. flux_2nd)
 """
 from __future__ import annotations
 
@@ -55,7 +61,7 @@ class _Cfg(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("wl", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("wr", ctypes.c_void_p),
                 ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int),
-                ("beta_mean", ctypes.c_int)]
+                ("beta_mean", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 def _load():
@@ -101,13 +107,21 @@ class Oracle:
     """
 
     def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
-                 gamma=1.4, eps=1e-36, p=2, flux="lf", beta_mean=False, candidates="gp"):
+                 gamma=1.4, eps=1e-36, p=2, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim",
+                 recon_weights=None):
+        """scheme "fdprim": GP-WENO Riemann states, face flux, high-order correction (Section 2,
+        Del Zanna's form); "fdflux": reconstruction of the split point fluxes (Section 2,
+        Shu-Osher's form) with reconstruction weights unless recon_weights=False (the naive
+        point-value weights of Eq. flux_2nd, kept for the order test)."""
         self.lib = _load()
         shape = tuple(int(s) for s in shape)
         self.ndim = len(shape)
         self.shape = shape
         self.nc = self.ndim + 2
-        t = gp_tables.scheme_tables(R, ell_over_dx, sigma_over_dx, poly=(candidates == "poly"))
+        if recon_weights is None:
+            recon_weights = scheme == "fdflux"
+        t = gp_tables.scheme_tables(R, ell_over_dx, sigma_over_dx, poly=(candidates == "poly"),
+                                    recon=bool(recon_weights))
         self.tables = t
         self._keep = [np.ascontiguousarray(t[k], dtype=np.float64) for k in ("wl", "gl", "wr", "gr", "Kinv")]
         c = _Cfg()
@@ -126,6 +140,7 @@ class Oracle:
         c.wl, c.gl, c.wr, c.gr, c.Kinv = [a.ctypes.data for a in self._keep]
         c.flux = {"lf": 0, "hllc": 1, "hll": 2}[flux]
         c.beta_mean = 1 if beta_mean else 0
+        c.scheme = {"fdprim": 0, "fdflux": 1}[scheme]
         self.cfg = c
         self.R = int(R)
         self.gamma = float(gamma)

@@ -61,6 +61,7 @@ typedef struct {
     const double *Kinv;/* [(R+1)][(R+1)] inverse of K_m built with sigma */
     int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC, 2 = HLL */
     int beta_mean;     /* 0 = zero-mean GP smoothness indicators (the paper's choice), 1 = mean f_centre */
+    int scheme;        /* 0 = FD-Prim (Riemann states + face flux + correction), 1 = FD-Flux (Section 2) */
 } oracle_cfg;
 
 static long ncells(const oracle_cfg *c) { return (long)c->n[0] * c->n[1] * c->n[2]; }
@@ -259,6 +260,25 @@ static void hll_flux(const double *uL, const double *uR, int nc, double g, doubl
     }
 }
 
+/* The 2R+2 cells s-R .. s+1+R along dimension d at transverse position cell,
+ * in normal-first component order (perm maps normal-first -> natural). */
+static void gather_stencil(const oracle_cfg *c, const double *U, int d, int s, const int cell[3], int perm[OR_MAXC],
+                           double st[OR_MAXS][OR_MAXC])
+{
+    int nc = c->ndim + 2, R = c->R, ns = 2 * R + 2;
+    long N = ncells(c);
+    perm[0] = 0; perm[1] = 1 + d;
+    int k = 2;
+    for (int a = 0; a < c->ndim; ++a) if (a != d) perm[k++] = 1 + a;
+    perm[nc - 1] = nc - 1;
+    for (int q = 0; q < ns; ++q) {
+        int idx[3] = { cell[0], cell[1], cell[2] };
+        idx[d] = map_index(c, d, s - R + q);
+        long l = lin(c, idx[0], idx[1], idx[2]);
+        for (int a = 0; a < nc; ++a) st[q][a] = U[(long)perm[a] * N + l];
+    }
+}
+
 /* Face flux F between cells s and s+1 along dimension d, at transverse
  * position (t1, t2) meaning the other two cell indices in natural order.
  * Writes nc values (natural component order).  Returns 0 on a non-physical
@@ -267,21 +287,9 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
                      double *uLout, double *uRout)
 {
     int nc = c->ndim + 2, R = c->R, ns = 2 * R + 2;
-    long N = ncells(c);
-    /* component permutation to normal-first ordering */
     int perm[OR_MAXC];
-    perm[0] = 0; perm[1] = 1 + d;
-    int k = 2;
-    for (int a = 0; a < c->ndim; ++a) if (a != d) perm[k++] = 1 + a;
-    perm[nc - 1] = nc - 1;
-
     double st[OR_MAXS][OR_MAXC];           /* stencil, normal-first, conserved */
-    for (int q = 0; q < ns; ++q) {
-        int idx[3] = { cell[0], cell[1], cell[2] };
-        idx[d] = map_index(c, d, s - R + q);
-        long l = lin(c, idx[0], idx[1], idx[2]);
-        for (int a = 0; a < nc; ++a) st[q][a] = U[(long)perm[a] * N + l];
-    }
+    gather_stencil(c, U, d, s, cell, perm, st);
     double roe[OR_MAXC + 1];
     if (!roe_average(st[R], st[R + 1], nc, c->gamma, roe)) return 0;
     double Rm[OR_MAXC][OR_MAXC], Lm[OR_MAXC][OR_MAXC];
@@ -336,6 +344,112 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
     return 1;
 }
 
+/* Right eigenvectors (columns of Rc) of the conservative normal-flux Jacobian
+ * dF/dU at velocity vel (normal first), total enthalpy H and sound speed c,
+ * waves in the order u-c, entropy, one shear wave per tangential velocity,
+ * u+c (textbook form):
+ *   (1, u - c e_n, H - u_n c), (1, u, |u|^2/2), (0, e_t, u_t), (1, u + c e_n, H + u_n c);
+ * the left eigenvectors Lc = Rc^{-1} by Gauss-Jordan elimination with partial
+ * pivoting.  Returns 0 if Rc is singular. */
+static int cons_eigensystem(const double *vel, double H, double c, int nc, double Rc[OR_MAXC][OR_MAXC],
+                            double Lc[OR_MAXC][OR_MAXC])
+{
+    int E = nc - 1, nv = nc - 2;
+    double q2 = 0.0;
+    for (int a = 0; a < nv; ++a) q2 += vel[a] * vel[a];
+    memset(Rc, 0, sizeof(double) * OR_MAXC * OR_MAXC);
+    Rc[0][0] = 1.0;
+    Rc[0][1] = 1.0;
+    Rc[0][E] = 1.0;
+    for (int a = 0; a < nv; ++a) {
+        Rc[1 + a][0] = vel[a] - (a == 0 ? c : 0.0);
+        Rc[1 + a][1] = vel[a];
+        Rc[1 + a][E] = vel[a] + (a == 0 ? c : 0.0);
+    }
+    Rc[E][0] = H - vel[0] * c;
+    Rc[E][1] = 0.5 * q2;
+    Rc[E][E] = H + vel[0] * c;
+    for (int t = 1; t < nv; ++t) {
+        Rc[1 + t][1 + t] = 1.0;
+        Rc[E][1 + t] = vel[t];
+    }
+    double A[OR_MAXC][2 * OR_MAXC];
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < 2 * nc; ++j) A[i][j] = j < nc ? Rc[i][j] : (j - nc == i ? 1.0 : 0.0);
+    for (int col = 0; col < nc; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < nc; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return 0;
+        for (int j = 0; j < 2 * nc; ++j) {
+            double t = A[col][j];
+            A[col][j] = A[piv][j];
+            A[piv][j] = t;
+        }
+        double inv = 1.0 / A[col][col];
+        for (int j = 0; j < 2 * nc; ++j) A[col][j] *= inv;
+        for (int r = 0; r < nc; ++r) {
+            if (r == col || A[r][col] == 0.0) continue;
+            double f = A[r][col];
+            for (int j = 0; j < 2 * nc; ++j) A[r][j] -= f * A[col][j];
+        }
+    }
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j) Lc[i][j] = A[i][nc + j];
+    return 1;
+}
+
+/* FD-Flux numerical flux at face s+1/2 (Section 2): the point fluxes F_j are
+ * read as cell averages of the function whose face value is the numerical
+ * flux (Eqs. prim_F, design), split by local Lax-Friedrichs into parts
+ * moving right and left, F^+- = (F +- alpha U)/2 with alpha = max over the
+ * 2R+2 stencil cells of |u_n| + c, projected on the characteristic fields
+ * of the conservative Jacobian at the Roe average of cells s and s+1, and
+ * reconstructed by GP-WENO: F^+ from the stencil of cell s at x* = +1/2,
+ * F^- from the stencil of cell s+1 at x* = -1/2 (the tables hold
+ * reconstruction weights).  Returns 0 on a non-physical state. */
+static int face_flux_fd(const oracle_cfg *c, const double *U, int d, int s, const int cell[3], double *Fout)
+{
+    int nc = c->ndim + 2, R = c->R, ns = 2 * R + 2;
+    int perm[OR_MAXC];
+    double st[OR_MAXS][OR_MAXC];
+    gather_stencil(c, U, d, s, cell, perm, st);
+    double roe[OR_MAXC + 1];
+    if (!roe_average(st[R], st[R + 1], nc, c->gamma, roe)) return 0;
+    double Rc[OR_MAXC][OR_MAXC], Lc[OR_MAXC][OR_MAXC];
+    if (!cons_eigensystem(&roe[1], roe[nc - 1], roe[nc], nc, Rc, Lc)) return 0;
+    double alpha = 0.0;
+    for (int q = 0; q < ns; ++q) {
+        double p = pressure(st[q], nc, c->gamma);
+        if (!(st[q][0] > 0.0) || !(p > 0.0)) return 0;
+        double a = fabs(st[q][1] / st[q][0]) + sqrt(c->gamma * p / st[q][0]);
+        if (a > alpha) alpha = a;
+    }
+    double gp[OR_MAXC][OR_MAXS], gm[OR_MAXC][OR_MAXS];
+    for (int q = 0; q < ns; ++q) {
+        double F[OR_MAXC];
+        normal_flux(st[q], nc, c->gamma, F);
+        for (int f = 0; f < nc; ++f) {
+            double v = 0.0, g = 0.0;
+            for (int a = 0; a < nc; ++a) {
+                v += Lc[f][a] * st[q][a];
+                g += Lc[f][a] * F[a];
+            }
+            gp[f][q] = 0.5 * (g + alpha * v);
+            gm[f][q] = 0.5 * (g - alpha * v);
+        }
+    }
+    double hat[OR_MAXC];
+    for (int f = 0; f < nc; ++f)
+        hat[f] = gp_weno(c, &gp[f][0], c->wl, c->gl) + gp_weno(c, &gm[f][1], c->wr, c->gr);
+    for (int a = 0; a < nc; ++a) {
+        double acc = 0.0;
+        for (int f = 0; f < nc; ++f) acc += Rc[a][f] * hat[f];
+        Fout[perm[a]] = acc;
+    }
+    return 1;
+}
+
 /* Corrected numerical flux at face s+1/2 from the five face fluxes
  * F_{s-3/2} .. F_{s+5/2} (Eqs. numFlux_cor and FD-ders, alpha = -1/24,
  * beta = 3/640; the Delta^2 and Delta^4 factors cancel). */
@@ -367,7 +481,8 @@ int oracle_rhs(const oracle_cfg *c, const double *U, double *dUdt)
                 int cell[3];
                 cell[t1] = a; cell[t2] = b; cell[d] = 0;
                 for (int s = -3; s <= n + 1; ++s)
-                    if (!face_flux(c, U, d, s, cell, &F[(s + 3) * nc], NULL, NULL)) {
+                    if (!(c->scheme == 1 ? face_flux_fd(c, U, d, s, cell, &F[(s + 3) * nc])
+                                         : face_flux(c, U, d, s, cell, &F[(s + 3) * nc], NULL, NULL))) {
                         bad = 1;
                         for (int q = 0; q < nc; ++q) F[(s + 3) * nc + q] = NAN;
                     }
@@ -380,7 +495,8 @@ int oracle_rhs(const oracle_cfg *c, const double *U, double *dUdt)
                             int s = i - 1 + side;   /* face s+1/2; F index of face t is t+3 */
                             double F5[5];
                             for (int e = 0; e < 5; ++e) F5[e] = F[(s + 1 + e) * nc + q];
-                            fh[side] = corrected_flux(F5);
+                            /* FD-Flux: the reconstructed flux is the numerical flux (Eq. design) */
+                            fh[side] = c->scheme == 1 ? F5[2] : corrected_flux(F5);
                         }
                         dUdt[(long)q * N + l] -= (fh[1] - fh[0]) / c->dx[d];
                     }

@@ -26,6 +26,19 @@ Tables returned (all numpy float64 after rounding the decimal results):
                 (Eq. beta-eigen), used only to pin the definition form.
 Sub-stencil m (0-based) holds the points -R+m .. m (Eq. sub-stencil with
 m_paper = m+1).
+
+Reconstruction tables (recon=True) serve the FD-Flux form of Section 2, where
+the point values F_j are read as cell averages of the function F^ whose face
+values are wanted (Eqs. prim_F, design).  The GP then conditions on cell
+averages: [C]_jk = covariance of the averages over cells j and k, [T]_j =
+covariance of the point x* with the average over cell j, and w = C^{-1} T.
+For the SE kernel (units of Delta, u = x - y):
+  G1(u) = int_0^u k = sqrt(pi/2) l erf(u / (sqrt(2) l))
+  G2(u) = int_0^u G1 = sqrt(pi/2) l u erf(u / (sqrt(2) l)) + l^2 (exp(-u^2/(2 l^2)) - 1)
+  C(delta) = G2(delta+1) - 2 G2(delta) + G2(delta-1)     (delta = x_j - x_k)
+  T_j = G1(x* - x_j + 1/2) - G1(x* - x_j - 1/2).
+Polynomial reconstruction weights (recon with poly) differentiate the
+Lagrange interpolant of the primitive function at the cell edges.
 """
 from __future__ import annotations
 
@@ -165,6 +178,101 @@ def m_matrix(w_sub, R):
     return M
 
 
+def pi_decimal():
+    """pi by Machin's formula, 16 atan(1/5) - 4 atan(1/239), with the atan Taylor series."""
+    with decimal.localcontext(_ctx()) as ctx:
+        ctx.prec = PREC + 10
+
+        def atan_inv(n):
+            x = Decimal(1) / n
+            x2 = x * x
+            term, total, k = x, x, 1
+            while True:
+                term *= -x2
+                add = term / (2 * k + 1)
+                if abs(add) < Decimal(10) ** (-(PREC + 5)):
+                    break
+                total += add
+                k += 1
+            return total
+
+        return +(16 * atan_inv(5) - 4 * atan_inv(239))
+
+
+def erf_decimal(z):
+    """erf(z) by its Maclaurin series 2/sqrt(pi) sum_n (-1)^n z^(2n+1) / (n! (2n+1))."""
+    with decimal.localcontext(_ctx()) as ctx:
+        ctx.prec = PREC + 30          # the alternating series cancels about e^(z^2)
+        z = _D(z)
+        z2 = z * z
+        term, total, n = z, z, 0
+        while True:
+            n += 1
+            term = -term * z2 / n
+            add = term / (2 * n + 1)
+            total += add
+            if abs(add) < Decimal(10) ** (-(PREC + 20)) and n > 2 * z2:
+                break
+        return +(2 / pi_decimal().sqrt() * total)
+
+
+def cell_average_cov(points, ell):
+    """[C]_jk: covariance of the cell averages over cells centred at points j, k (width 1)."""
+    with decimal.localcontext(_ctx()):
+        rt = (pi_decimal() / 2).sqrt() * ell
+        s2l = Decimal(2).sqrt() * ell
+
+        def G2(u):
+            return rt * u * erf_decimal(u / s2l) + ell * ell * ((-(u * u) / (2 * ell * ell)).exp() - 1)
+
+        return [[G2(a - b + 1) - 2 * G2(a - b) + G2(a - b - 1) for b in points] for a in points]
+
+
+def point_cell_cov(points, xs, ell):
+    """[T]_j: covariance of the point value at xs with the average over the cell centred at points j."""
+    with decimal.localcontext(_ctx()):
+        rt = (pi_decimal() / 2).sqrt() * ell
+        s2l = Decimal(2).sqrt() * ell
+
+        def G1(u):
+            return rt * erf_decimal(u / s2l)
+
+        half = Decimal(1) / 2
+        return [G1(xs - b + half) - G1(xs - b - half) for b in points]
+
+
+def gp_recon_weights(points, xs, ell):
+    """w = C^{-1} T: GP prediction of the point value at xs from cell averages."""
+    return solve(cell_average_cov(points, ell), point_cell_cov(points, xs, ell))
+
+
+def poly_recon_weights(points, xs):
+    """Polynomial reconstruction at xs from cell averages on unit cells centred at points:
+    the primitive P(e_m) = sum_{j<m} avg_j at the S+1 edges e_m is interpolated and
+    differentiated, so w_j = sum_{m>j} L'_m(xs)."""
+    with decimal.localcontext(_ctx()):
+        half = Decimal(1) / 2
+        edges = [points[0] - half] + [p + half for p in points]
+        ne = len(edges)
+        dL = []
+        for m in range(ne):
+            den = Decimal(1)
+            for l in range(ne):
+                if l != m:
+                    den *= edges[m] - edges[l]
+            num = Decimal(0)
+            for l in range(ne):
+                if l == m:
+                    continue
+                prod = Decimal(1)
+                for q in range(ne):
+                    if q != m and q != l:
+                        prod *= xs - edges[q]
+                num += prod
+            dL.append(num / den)
+        return [sum(dL[j + 1:], Decimal(0)) for j in range(len(points))]
+
+
 def lagrange_weights(points, xs):
     """Lagrange basis values l_j(x*) = prod_{k != j} (x* - x_k) / (x_j - x_k) (polynomial interpolation)."""
     with decimal.localcontext(_ctx()):
@@ -179,10 +287,13 @@ def lagrange_weights(points, xs):
 
 
 @lru_cache(maxsize=None)
-def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str, poly: bool = False):
+def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str, poly: bool = False, recon: bool = False):
     ell, sigma, xs = Decimal(ell_s), Decimal(sigma_s), Decimal(xs_s)
     big = [Decimal(j) for j in range(-R, R + 1)]
-    weights = lagrange_weights if poly else (lambda pts, x: gp_weights(pts, x, ell))
+    if recon:
+        weights = poly_recon_weights if poly else (lambda pts, x: gp_recon_weights(pts, x, ell))
+    else:
+        weights = lagrange_weights if poly else (lambda pts, x: gp_weights(pts, x, ell))
     w_big = weights(big, xs)
     w_sub = []
     for m in range(R + 1):
@@ -199,13 +310,15 @@ def _tables_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str, poly: bool = Fa
                 lam_sigma=lam, V_sigma=V, K_ell=covariance(big, ell))
 
 
-def tables_decimal(R: int, ell_over_dx, sigma_over_dx, xstar, poly=False):
+def tables_decimal(R: int, ell_over_dx, sigma_over_dx, xstar, poly=False, recon=False):
     """Decimal tables (see module docstring) for one prediction point x* in units of Delta.
     poly=True: polynomial (Lagrange) candidate and big-stencil weights instead of the GP
     weights -- the WENO-GP hybrid of the paper's WENO-JS comparison (GP smoothness
     indicators on polynomial candidates); the linear weights then solve Eq. gamm-system
-    for those weights."""
-    return _tables_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)), bool(poly))
+    for those weights.  recon=True: weights that predict the point value from cell
+    averages (FD-Flux, Section 2); the smoothness-indicator tables are unchanged."""
+    return _tables_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)), bool(poly),
+                           bool(recon))
 
 
 def _f64(x):
@@ -214,19 +327,21 @@ def _f64(x):
     return float(x)
 
 
-def tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5, poly: bool = False) -> dict:
+def tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5, poly: bool = False,
+           recon: bool = False) -> dict:
     """The same tables rounded to float64 numpy arrays."""
-    t = tables_decimal(R, ell_over_dx, sigma_over_dx, xstar, poly)
+    t = tables_decimal(R, ell_over_dx, sigma_over_dx, xstar, poly, recon)
     out = {k: _f64(v) for k, v in t.items()}
     out["R"] = int(R)
     return out
 
 
-def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, poly: bool = False) -> dict:
+def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, poly: bool = False,
+                  recon: bool = False) -> dict:
     """Everything the per-face oracle needs: left-state tables (x* = +1/2 from
     the stencil of cell i), right-state tables (x* = -1/2 from the stencil of
     cell i+1, computed directly, not by reversal) and K_m(sigma)^{-1}."""
-    tl = tables(R, ell_over_dx, sigma_over_dx, 0.5, poly)
-    tr = tables(R, ell_over_dx, sigma_over_dx, -0.5, poly)
+    tl = tables(R, ell_over_dx, sigma_over_dx, 0.5, poly, recon)
+    tr = tables(R, ell_over_dx, sigma_over_dx, -0.5, poly, recon)
     return dict(R=int(R), wl=tl["w_sub"], gl=tl["gamma"], wr=tr["w_sub"], gr=tr["gamma"],
                 Kinv=tl["Kinv_sigma"], w_big_l=tl["w_big"], w_big_r=tr["w_big"])
