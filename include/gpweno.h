@@ -86,7 +86,17 @@ typedef struct {
  *   candidates     0 = GP candidate predictions (Eq. candidate_interp);
  *                  1 = polynomial (Lagrange) candidates and their linear
  *                  weights with the GP smoothness indicators (the paper's
- *                  WENO-GP hybrid). */
+ *                  WENO-GP hybrid).
+ *   scheme         0 = FD-Prim (default): GP-WENO Riemann states at faces,
+ *                  face flux, high-order correction (Eqs. riemann_prob,
+ *                  numFlux_cor).  1 = FD-Flux (Section 2): the point fluxes are
+ *                  read as cell averages of the function whose face values are
+ *                  the numerical fluxes (Eqs. prim_F, design); they are split by
+ *                  local Lax-Friedrichs, F+- = (F +- alpha U)/2 with alpha the
+ *                  largest |u_n| + c over the face's 2R+2 stencil cells, projected
+ *                  on the characteristic fields of the conservative Jacobian at
+ *                  the Roe average, and reconstructed with GP weights conditioned
+ *                  on cell averages; no correction.  Requires flux_form = 0. */
 typedef struct {
     double sigma_over_dx;
     double eps;
@@ -96,6 +106,7 @@ typedef struct {
     int flux_form;
     int beta_mean;
     int candidates;
+    int scheme;
 } gpweno_opts;
 
 void gpweno_default_opts(gpweno_opts *opts);
@@ -128,12 +139,13 @@ gpweno_status gpweno_plan_tables(gpweno_plan plan, double *w_m, double *gam, dou
 
 /* Host-only: the double-double GP tables of gpweno_plan_create without a
  * plan or a device (for checking the precompute on machines without a GPU).
- * `candidates` as in gpweno_opts.  Left-state tables as in gpweno_plan_tables; w_m_r, gam_r are the tables
+ * `candidates` and `scheme` as in gpweno_opts (scheme 1: reconstruction weights).
+ * Left-state tables as in gpweno_plan_tables; w_m_r, gam_r are the tables
  * of the right state of face i+1/2 (x* = x_{i+1} - dx/2, stencil of cell
  * i+1).  Any output pointer may be NULL.  Returns GPWENO_ERR_ARG or
  * GPWENO_ERR_PRECOMPUTE as gpweno_plan_create would. */
-gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, double *w_m,
-                               double *gam, double *P, double *w_big, double *w_m_r, double *gam_r);
+gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, int scheme,
+                               double *w_m, double *gam, double *P, double *w_big, double *w_m_r, double *gam_r);
 
 /* dUdt = L(U): the right-hand side of Eq. disc_fd with the corrected fluxes
  * of Eq. numFlux_cor.  U, dUdt: device state arrays (see conventions);
@@ -186,8 +198,9 @@ gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 /* Batched 2D stepping (same per-face scheme as gpweno_rk3_step): one
  * persistent launch per RK stage serves n independent 2D plans of possibly
  * different grid size, R, l/dx, sigma, face flux, candidates and boundary
- * conditions (all plans must share dtype and device and use beta_mean = 0,
- * else GPWENO_ERR_ARG; at most 12 distinct table sets per radius).  The host cuts every
+ * conditions (all plans must share dtype and device and use beta_mean = 0
+ * and scheme = 0, else GPWENO_ERR_ARG; at most 12 distinct table sets per
+ * radius).  The host cuts every
  * instance into strips and row segments and hands each CTA a contiguous run of
  * segments of equal estimated cost.  The batch refers to the member plans,
  * which must outlive it.  tune_cache: NULL, or the path of a text file of

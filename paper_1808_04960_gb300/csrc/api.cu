@@ -64,6 +64,7 @@ void gpweno_default_opts(gpweno_opts *o)
     o->flux_form = 0;
     o->beta_mean = 0;
     o->candidates = 0;
+    o->scheme = 0;
 }
 
 const char *gpweno_last_error(void) { return g_err; }
@@ -103,6 +104,14 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     }
     if ((o.beta_mean != 0 && o.beta_mean != 1) || (o.candidates != 0 && o.candidates != 1)) {
         set_error("beta_mean=%d and candidates=%d must each be 0 or 1", o.beta_mean, o.candidates);
+        return GPWENO_ERR_ARG;
+    }
+    if (o.scheme != 0 && o.scheme != 1) {
+        set_error("scheme=%d: 0 (FD-Prim) or 1 (FD-Flux)", o.scheme);
+        return GPWENO_ERR_ARG;
+    }
+    if (o.scheme == 1 && o.flux_form != 0) {
+        set_error("scheme=1 (FD-Flux) splits the fluxes itself; flux_form must be 0, got %d", o.flux_form);
         return GPWENO_ERR_ARG;
     }
     if (o.flux_form < 0 || o.flux_form > 2) {
@@ -151,7 +160,7 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     p->opts = o;
     p->ncell = ncell;
     char err[256];
-    int rc = gp_precompute(R, ell_over_dx, o.sigma_over_dx, &p->tab, err, sizeof(err), o.candidates);
+    int rc = gp_precompute(R, ell_over_dx, o.sigma_over_dx, &p->tab, err, sizeof(err), o.candidates, o.scheme);
     if (rc) {
         set_error("%s", err);
         delete p;
@@ -196,16 +205,16 @@ gpweno_status gpweno_plan_tables(gpweno_plan p, double *w_m, double *gam, double
     return GPWENO_OK;
 }
 
-gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, double *w_m,
-                               double *gam, double *P, double *w_big, double *w_m_r, double *gam_r)
+gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, int candidates, int scheme,
+                               double *w_m, double *gam, double *P, double *w_big, double *w_m_r, double *gam_r)
 {
     GpTables t;
     char err[256];
-    if (candidates != 0 && candidates != 1) {
-        set_error("candidates=%d must be 0 or 1", candidates);
+    if ((candidates != 0 && candidates != 1) || (scheme != 0 && scheme != 1)) {
+        set_error("candidates=%d and scheme=%d must each be 0 or 1", candidates, scheme);
         return GPWENO_ERR_ARG;
     }
-    int rc = gp_precompute(R, ell_over_dx, sigma_over_dx, &t, err, sizeof(err), candidates);
+    int rc = gp_precompute(R, ell_over_dx, sigma_over_dx, &t, err, sizeof(err), candidates, scheme);
     if (rc) {
         set_error("%s", err);
         return rc == 1 ? GPWENO_ERR_ARG : GPWENO_ERR_PRECOMPUTE;
@@ -366,8 +375,8 @@ gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int 
             set_error("gpweno_plan_batch: plan %d is not a 2D single-grid plan", k);
             return GPWENO_ERR_ARG;
         }
-        if (p->opts.beta_mean) {
-            set_error("gpweno_plan_batch: plan %d uses beta_mean = 1, which batches do not support", k);
+        if (p->opts.beta_mean || p->opts.scheme) {
+            set_error("gpweno_plan_batch: plan %d uses beta_mean = 1 or scheme = 1, which batches do not support", k);
             return GPWENO_ERR_ARG;
         }
         if (p->opts.dtype != plans[0]->opts.dtype || p->device != plans[0]->device) {

@@ -69,9 +69,10 @@ StageArgs<T> base_args(const gpweno_plan_s *p)
     return a;
 }
 
-// MEAN: the non-zero-mean smoothness indicators (beta on f - f_centre), a
-// compile-time switch so that the default kernels keep their register budget.
-template <typename T, int R, bool MEAN>
+// VAR: the scheme variant (kVarMean: non-zero-mean smoothness indicators,
+// kVarFdFlux: the FD-Flux form), a compile-time switch so that the default
+// kernels keep their register budget.
+template <typename T, int R, int VAR>
 gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t st)
 {
     StageArgs<T> a = a0;
@@ -81,7 +82,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         // (1) xy-plane kernel: P = -(div_x/dx + div_y/dy)
         {
             const size_t smem = stage2d_smem_bytes<T, R, NT, 5>();
-            auto kern = plane3d_kernel<T, R, NT, MEAN>;
+            auto kern = plane3d_kernel<T, R, NT, VAR>;
             static int occ = 0;
             if (!occ) {
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -107,7 +108,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         // (2) z-marching kernel: L = P - div_z/dz and the stage update
         {
             const size_t smem = stagez_smem_bytes<T, R, NT>();
-            auto kern = stagez_kernel<T, R, NT, MEAN>;
+            auto kern = stagez_kernel<T, R, NT, VAR>;
             static int occ = 0;
             if (!occ) {
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -123,7 +124,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     } else if (p->dims.ndim == 2) {
         constexpr int NT = kNT2D;
         const size_t smem = stage2d_smem_bytes<T, R, NT>();
-        auto kern = stage2d_kernel<T, R, NT, MEAN>;
+        auto kern = stage2d_kernel<T, R, NT, VAR>;
         static int occ = 0;   // per instantiation: resident CTAs per SM
         if (!occ) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -142,7 +143,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     } else {
         constexpr int NT = kNT1D;
         const size_t smem = stage1d_smem_bytes<T, R, NT>();
-        auto kern = stage1d_kernel<T, R, NT, MEAN>;
+        auto kern = stage1d_kernel<T, R, NT, VAR>;
         a.nstrips = (a.n[0] + (NT - 5) - 1) / (NT - 5);
         a.W = (a.n[0] + a.nstrips - 1) / a.nstrips;
         a.H = 1;
@@ -155,7 +156,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     return GPWENO_OK;
 }
 
-template <typename T, bool MEAN>
+template <typename T, int VAR>
 gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
     StageArgs<T> a = base_args<T>(p);
@@ -174,9 +175,9 @@ gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
     a.dt_dev = io.dt_dev;
     a.rate = io.want_rate ? p->ws : nullptr;
     switch (p->R) {
-    case 1: return launch_stage_R<T, 1, MEAN>(p, a, st);
-    case 2: return launch_stage_R<T, 2, MEAN>(p, a, st);
-    case 3: return launch_stage_R<T, 3, MEAN>(p, a, st);
+    case 1: return launch_stage_R<T, 1, VAR>(p, a, st);
+    case 2: return launch_stage_R<T, 2, VAR>(p, a, st);
+    case 3: return launch_stage_R<T, 3, VAR>(p, a, st);
     default: set_error("R=%d not compiled", p->R); return GPWENO_ERR_ARG;
     }
 }

@@ -149,6 +149,135 @@ __device__ __forceinline__ bool prim_pert(const PrimRef<T, NC> &r, const T (&w)[
     return (rho > T(0)) && (pr > T(0));
 }
 
+// Roe average of the two cells sharing a face (normal-first conserved uL =
+// cell s, uR = cell s+1), the primitive eigen-system at it, and cell s as the
+// primitive reference of the cell-relative evaluation:
+//   L_V rows: (0, -an, 0, ap), (1, 0, 0, -ie), e_t, (0, an, 0, ap)
+//   R_V cols: (1, -cr, 0, c^2), (1, 0, 0, 0),   e_t, (1, cr, 0, c^2)
+// with an = rbar/(2c), ap = 1/(2c^2), ie = 1/c^2, cr = c/rbar, rbar = sqrt(rho_L rho_R).
+template <typename T, int NC>
+struct FaceRoe {
+    static constexpr int NV = NC - 2, E = NC - 1;
+    T gm1, igm1;
+    T vel[NV];        // Roe velocity
+    T q2;             // |vel|^2
+    T c2, c, ic;      // Roe sound speed squared, sound speed, 1/c
+    T rbar, irb;      // sqrt(rho_L rho_R) and its inverse
+    T an, ie, ap, cr;
+    PrimRef<T, NC> ref;
+    T Vs[NC];         // primitive state of cell s
+    bool ok;          // rho_L, rho_R, c^2 > 0
+
+    // row kk of L_V applied to a primitive vector
+    __device__ __forceinline__ T lrow(int kk, const T *v) const
+    {
+        if (kk == 0) return fma(ap, v[E], -an * v[1]);
+        if (kk == E) return fma(ap, v[E], an * v[1]);
+        if (kk == 1) return fma(-ie, v[E], v[0]);
+        return v[kk];   // shear: tangential velocity
+    }
+
+    // V_j - V_s from the exact conserved difference U_j - U_s by perturbation algebra
+    __device__ __forceinline__ void prim_diff(const T (&uj)[NC], const T (&us)[NC], T (&dV)[NC]) const
+    {
+        T dU[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) dU[a] = uj[a] - us[a];
+        const T irj = Num<T>::rcp(uj[0]);
+        T k = T(0);
+        dV[0] = dU[0];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            const T du = fma(-ref.u[a], dU[0], dU[1 + a]) * irj;
+            dV[1 + a] = du;
+            k = fma(uj[1 + a], du, fma(ref.u[a], dU[1 + a], k));
+        }
+        dV[E] = gm1 * fma(T(-0.5), k, dU[E]);
+    }
+};
+
+template <typename T, int NC>
+__device__ __forceinline__ FaceRoe<T, NC> face_roe(const T (&uL)[NC], const T (&uR)[NC], T gamma)
+{
+    constexpr int NV = NC - 2, E = NC - 1;
+    FaceRoe<T, NC> f;
+    f.gm1 = gamma - T(1);
+    f.igm1 = Num<T>::rcp(f.gm1);
+    const T rL = uL[0], rR = uR[0];
+    const T rsL = Num<T>::rsqrt(rL), rsR = Num<T>::rsqrt(rR);
+    const T inv = Num<T>::rcp(rL * rsL + rR * rsR);  // 1/(sqrt(rhoL)+sqrt(rhoR))
+    const T irL = rsL * rsL;
+    T q2 = T(0), mL2 = T(0), mR2 = T(0);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        f.vel[a] = fma(uL[1 + a], rsL, uR[1 + a] * rsR) * inv;
+        q2 = fma(f.vel[a], f.vel[a], q2);
+        mL2 = fma(uL[1 + a], uL[1 + a], mL2);
+        mR2 = fma(uR[1 + a], uR[1 + a], mR2);
+    }
+    const T pL = f.gm1 * fma(T(-0.5) * mL2, irL, uL[E]);
+    const T pR = f.gm1 * fma(T(-0.5) * mR2, rsR * rsR, uR[E]);
+    const T H = fma(uL[E] + pL, rsL, (uR[E] + pR) * rsR) * inv;
+    f.q2 = q2;
+    f.c2 = f.gm1 * fma(T(-0.5), q2, H);
+    f.ok = (rL > T(0)) && (rR > T(0)) && (f.c2 > T(0));
+    f.ic = Num<T>::rsqrt(Num<T>::fmax(f.c2, T(1e-30)));
+    f.c = f.c2 * f.ic;
+    f.rbar = (rL * rsL) * (rR * rsR);
+    f.irb = rsL * rsR;
+    f.an = T(0.5) * f.rbar * f.ic;
+    f.ie = f.ic * f.ic;
+    f.ap = T(0.5) * f.ie;
+    f.cr = f.c * f.irb;
+    f.ref.rho = rL;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) f.ref.u[a] = uL[1 + a] * irL;
+    f.ref.p = pL;
+    f.ref.hp = uL[E] + pL;
+    f.ref.mn = uL[1];
+    f.Vs[0] = rL;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) f.Vs[1 + a] = f.ref.u[a];
+    f.Vs[E] = pL;
+    return f;
+}
+
+// (eps + beta)^-p of one smoothness window: beta = sum_h (P_h . (f - shift))^2
+// (Eq. beta-eigen) over the window f[w..w+R] of data f_j = f_c + d_j with
+// d_R = 0 (relative to the face's cell s).  pf_h = (f_c - shift) sum_j P_hj is
+// supplied by the caller (zero for the skew rows, whose sums vanish); rows are
+// evaluated in the symmetric/skew half form.
+template <typename T, int R, int NS>
+__device__ __forceinline__ T beta_weight(const FaceTables<T, R> &tb, const T (&d)[NS], int w, const T (&pf)[R + 1])
+{
+    constexpr int S = R + 1, HALF = S / 2;
+    T ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+        const int lo = w + j, hi = w + S - 1 - j;
+        ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : d[lo] + d[hi]);
+        ms[j] = lo == R ? -d[hi] : (hi == R ? d[lo] : d[lo] - d[hi]);
+    }
+    T beta = T(0);
+#pragma unroll
+    for (int h = 0; h < S; ++h) {
+        T dot;
+        if (h % 2 == 0) {
+            dot = pf[h];
+            if (S % 2 == 1 && w + HALF != R) dot = fma(tb.Ph[h][HALF], d[w + HALF], dot);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) dot = fma(tb.Ph[h][j], ps[j], dot);
+        } else {
+            dot = tb.Ph[h][0] * ms[0];
+#pragma unroll
+            for (int j = 1; j < HALF; ++j) dot = fma(tb.Ph[h][j], ms[j], dot);
+        }
+        beta = fma(dot, dot, beta);
+    }
+    const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(tb.eps, beta), Num<T>::eps_floor()));
+    return tb.p == 2 ? Num<T>::mul_rn(x, x) : x;
+}
+
 // One face, cell-relative form.  st[0..2R+1] is the normal-first conserved
 // stencil; the face s+1/2 lies between st[R] (cell s) and st[R+1] (cell s+1).
 // Outputs
@@ -175,53 +304,12 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
 {
     constexpr int NS = 2 * R + 2;
     constexpr int E = NC - 1;
-    constexpr int NV = NC - 2;
-    constexpr int S = R + 1, HALF = S / 2;
-    const T gm1 = tb.gamma - T(1);
-    const T igm1 = Num<T>::rcp(gm1);
-
-    // --- Roe average of the two cells sharing the face -------------------
-    const T rL = st[R][0], rR = st[R + 1][0];
-    const T rsL = Num<T>::rsqrt(rL), rsR = Num<T>::rsqrt(rR);
-    const T inv = Num<T>::rcp(rL * rsL + rR * rsR);  // 1/(sqrt(rhoL)+sqrt(rhoR))
-    const T irL = rsL * rsL;
-    T vel[NV];
-    T q2 = T(0), mL2 = T(0), mR2 = T(0);
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-        vel[a] = fma(st[R][1 + a], rsL, st[R + 1][1 + a] * rsR) * inv;
-        q2 = fma(vel[a], vel[a], q2);
-        mL2 = fma(st[R][1 + a], st[R][1 + a], mL2);
-        mR2 = fma(st[R + 1][1 + a], st[R + 1][1 + a], mR2);
-    }
-    const T pL = gm1 * fma(T(-0.5) * mL2, irL, st[R][E]);
-    const T pR = gm1 * fma(T(-0.5) * mR2, rsR * rsR, st[R + 1][E]);
-    const T H = fma(st[R][E] + pL, rsL, (st[R + 1][E] + pR) * rsR) * inv;
-    const T c2 = gm1 * fma(T(-0.5), q2, H);
-    bool ok = (rL > T(0)) && (rR > T(0)) && (c2 > T(0));
-    const T ic = Num<T>::rsqrt(Num<T>::fmax(c2, T(1e-30)));
-    const T c = c2 * ic;
-    const T rbar = (rL * rsL) * (rR * rsR);   // sqrt(rhoL rhoR)
-    const T irb = rsL * rsR;                  // 1/rbar
-    // primitive eigenvectors at (rbar, c):
-    //   L rows: (0, -an, 0, ap), (1, 0, 0, -ie), e_t, (0, an, 0, ap)
-    //   R cols: (1, -c/rbar, 0, c^2), (1, 0, 0, 0), e_t, (1, c/rbar, 0, c^2)
-    const T an = T(0.5) * rbar * ic, ie = ic * ic, ap = T(0.5) * ie;
-    const T cr = c * irb;
-
-    // primitive reference: cell s
-    PrimRef<T, NC> ref;
-    ref.rho = rL;
-#pragma unroll
-    for (int a = 0; a < NV; ++a) ref.u[a] = st[R][1 + a] * irL;
-    ref.p = pL;
-    ref.hp = st[R][E] + pL;
-    ref.mn = st[R][1];
-    T Vs[NC];
-    Vs[0] = rL;
-#pragma unroll
-    for (int a = 0; a < NV; ++a) Vs[1 + a] = ref.u[a];
-    Vs[E] = pL;
+    constexpr int S = R + 1;
+    const FaceRoe<T, NC> f = face_roe<T, NC>(st[R], st[R + 1], tb.gamma);
+    bool ok = f.ok;
+    const T igm1 = f.igm1, c = f.c, c2 = f.c2, cr = f.cr;
+    const PrimRef<T, NC> &ref = f.ref;
+    const T(&vel)[NC - 2] = f.vel;
 
     // primitive differences V_j - V_s from the exact conserved differences
     T dV[NS][NC];
@@ -232,68 +320,17 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             for (int a = 0; a < NC; ++a) dV[j][a] = T(0);
             continue;
         }
-        T dU[NC];
-#pragma unroll
-        for (int a = 0; a < NC; ++a) dU[a] = st[j][a] - st[R][a];
-        const T irj = Num<T>::rcp(st[j][0]);
-        T k = T(0);
-        dV[j][0] = dU[0];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) {
-            const T du = fma(-ref.u[a], dU[0], dU[1 + a]) * irj;
-            dV[j][1 + a] = du;
-            k = fma(st[j][1 + a], du, fma(ref.u[a], dU[1 + a], k));
-        }
-        dV[j][E] = gm1 * fma(T(-0.5), k, dU[E]);
+        f.prim_diff(st[j], st[R], dV[j]);
     }
-
-    // row k of L_V applied to a primitive vector
-    auto lrow = [&](int kk, const T *v) -> T {
-        if (kk == 0) return fma(ap, v[E], -an * v[1]);
-        if (kk == E) return fma(ap, v[E], an * v[1]);
-        if (kk == 1) return fma(-ie, v[E], v[0]);
-        return v[kk];   // shear: tangential velocity
-    };
 
     T dqL[NC], dqR[NC];
 #pragma unroll
     for (int kk = 0; kk < NC; ++kk) {
-        const T fc = lrow(kk, Vs);
+        const T fc = f.lrow(kk, f.Vs);
         T d[NS];
 #pragma unroll
-        for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : lrow(kk, dV[j]);
+        for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : f.lrow(kk, dV[j]);
 
-        // --- smoothness indicators ------------------------------------------
-        // beta over window d[w..w+R] with the data shifted by a constant c (P_h . (f - c) =
-        // P_h . d + (f_c - c) sum_j P_hj; only the symmetric rows have a non-zero sum):
-        // returns (eps + beta)^-p
-        auto beta_x = [&](int w, const T (&pf)[S]) -> T {
-            T ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
-#pragma unroll
-            for (int j = 0; j < HALF; ++j) {
-                const int lo = w + j, hi = w + S - 1 - j;
-                ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : d[lo] + d[hi]);
-                ms[j] = lo == R ? -d[hi] : (hi == R ? d[lo] : d[lo] - d[hi]);
-            }
-            T beta = T(0);
-#pragma unroll
-            for (int h = 0; h < S; ++h) {
-                T dot;
-                if (h % 2 == 0) {
-                    dot = pf[h];
-                    if (S % 2 == 1 && w + HALF != R) dot = fma(tb.Ph[h][HALF], d[w + HALF], dot);
-#pragma unroll
-                    for (int j = 0; j < HALF; ++j) dot = fma(tb.Ph[h][j], ps[j], dot);
-                } else {
-                    dot = tb.Ph[h][0] * ms[0];
-#pragma unroll
-                    for (int j = 1; j < HALF; ++j) dot = fma(tb.Ph[h][j], ms[j], dot);
-                }
-                beta = fma(dot, dot, beta);
-            }
-            const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(tb.eps, beta), Num<T>::eps_floor()));
-            return tb.p == 2 ? Num<T>::mul_rn(x, x) : x;
-        };
         // zero mean: both sides shift by f_c, so the right side's window m is the
         // left side's window m+1 and the R+2 windows are shared.  Mean f_centre:
         // the left side's centre is cell s (no shift), the right side's is cell
@@ -307,10 +344,10 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
         // --- candidates relative to the centre cells and nonlinear weights ---
         // omega_m ~ gamma_m (eps + beta_m)^-p  (Eq. weights); sum_m omega_m = 1 is used exactly.
         T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
-        T xl = beta_x(0, pfl);
+        T xl = beta_weight<T, R, NS>(tb, d, 0, pfl);
 #pragma unroll
         for (int m = 0; m <= R; ++m) {
-            const T xr = beta_x(m + 1, pfr);
+            const T xr = beta_weight<T, R, NS>(tb, d, m + 1, pfr);
             T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
 #pragma unroll
             for (int j = 0; j <= R; ++j) {
@@ -323,7 +360,7 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             denL = Num<T>::add_rn(denL, yl);
             numR = fma(yr, sr, numR);
             denR = Num<T>::add_rn(denR, yr);
-            if (m < R) xl = MEAN ? beta_x(m + 1, pfl) : xr;
+            if (m < R) xl = MEAN ? beta_weight<T, R, NS>(tb, d, m + 1, pfl) : xr;
         }
         dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
         dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}
@@ -412,6 +449,157 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
     return ok;
 }
 
+// One face of the FD-Flux form (Section 2), cell-relative; outputs as face_rel:
+//   A = f^_{s+1/2} - F(U_s),  B = F(U_{s+1}) - F(U_s).
+// The point fluxes are cell averages of the function whose face values are
+// the numerical fluxes (Eqs. prim_F, design).  They are split by local
+// Lax-Friedrichs, F+- = (F +- alpha U)/2 with alpha the largest |u_n| + c over
+// the 2R+2 stencil cells, projected on the characteristic fields of the
+// conservative Jacobian at the Roe average, l(X) = L_V (dV/dU) X with dV/dU
+// taken at (rbar, vel, c) (the conservative Jacobian depends on the state only
+// through vel and H, so these are its left eigenvectors up to row scaling),
+// reconstructed by GP-WENO -- F+ on the stencil of cell s at x* = +1/2, F- on
+// that of cell s+1 at x* = -1/2, the tables holding reconstruction weights --
+// and projected back with (dU/dV) R_V.  Everything is relative to cell s:
+// with d+-_j = (l(F_j - F_s) +- alpha l(U_j - U_s)) / 2 and g+-_s the cell-s
+// values, each reconstructed part minus g+-_s is
+// sum_m omega_m (w_m . d_m + (sum_j w_mj - 1) g+-_s), and g+_s + g-_s = l(F_s)
+// projects back to F(U_s).  Returns false on a non-physical state.
+template <typename T, int NC, int R, bool MEAN = false>
+__device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
+                                         T (&B)[NC])
+{
+    constexpr int NS = 2 * R + 2, E = NC - 1, NV = NC - 2, S = R + 1;
+    const FaceRoe<T, NC> f = face_roe<T, NC>(st[R], st[R + 1], tb.gamma);
+    bool ok = f.ok;
+
+    // splitting speed: the largest |u_n| + c over the stencil
+    T alpha = T(0);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const T ir = Num<T>::rcp(st[j][0]);
+        T m2 = T(0);
+#pragma unroll
+        for (int a = 0; a < NV; ++a) m2 = fma(st[j][1 + a], st[j][1 + a], m2);
+        const T pj = f.gm1 * fma(T(-0.5) * m2, ir, st[j][E]);
+        ok = ok && (st[j][0] > T(0)) && (pj > T(0));
+        alpha = Num<T>::fmax(alpha, Num<T>::fabs(st[j][1] * ir) +
+                                        Num<T>::sqrt(Num<T>::fmax(tb.gamma * pj * ir, T(0))));
+    }
+    // dV/dU at the Roe state applied to a conserved vector
+    auto jac = [&](const T (&X)[NC], T (&Y)[NC]) {
+        Y[0] = X[0];
+        T k = T(0);
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            Y[1 + a] = fma(-f.vel[a], X[0], X[1 + a]) * f.irb;
+            k = fma(f.vel[a], X[1 + a], k);
+        }
+        Y[E] = f.gm1 * (fma(T(0.5) * f.q2, X[0], X[E]) - k);
+    };
+    // cell s: U_s and F(U_s)
+    T Fs[NC];
+    Fs[0] = st[R][1];
+    Fs[1] = fma(st[R][1], f.ref.u[0], f.ref.p);
+#pragma unroll
+    for (int a = 1; a < NV; ++a) Fs[1 + a] = st[R][1] * f.ref.u[a];
+    Fs[E] = f.ref.u[0] * f.ref.hp;
+    T JUs[NC], JFs[NC];
+    jac(st[R], JUs);
+    jac(Fs, JFs);
+
+    // characteristic increments of the split fluxes, relative to cell s
+    T dp[NC][NS], dm[NC][NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        if (j == R) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) dp[k][j] = dm[k][j] = T(0);
+            continue;
+        }
+        T dV[NC], G[NC], cw[NC], un, cs;
+        f.prim_diff(st[j], st[R], dV);
+        ok = prim_pert<T, NC>(f.ref, dV, tb.gamma, f.igm1, G, cw, un, cs) && ok;
+        if (j == R + 1) {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) B[a] = G[a];
+        }
+        T dU[NC], JdU[NC], JG[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) dU[a] = st[j][a] - st[R][a];
+        jac(dU, JdU);
+        jac(G, JG);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const T lg = f.lrow(k, JG), lv = f.lrow(k, JdU);
+            dp[k][j] = T(0.5) * fma(alpha, lv, lg);
+            dm[k][j] = T(0.5) * fma(-alpha, lv, lg);
+        }
+    }
+
+    T dq[NC];
+#pragma unroll
+    for (int kk = 0; kk < NC; ++kk) {
+        const T lgs = f.lrow(kk, JFs), lvs = f.lrow(kk, JUs);
+        const T fcp = T(0.5) * fma(alpha, lvs, lgs), fcm = T(0.5) * fma(-alpha, lvs, lgs);
+        // zero mean: shifts g+_s and g-_s; mean: centres cell s (left) and s+1 (right)
+        T pfl[S], pfr[S];
+#pragma unroll
+        for (int h = 0; h < S; ++h) {
+            pfl[h] = (h % 2 == 0 && !MEAN) ? tb.Psum[h] * fcp : T(0);
+            pfr[h] = (h % 2 == 0) ? (MEAN ? -tb.Psum[h] * dm[kk][R + 1] : tb.Psum[h] * fcm) : T(0);
+        }
+        T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
+#pragma unroll
+        for (int m = 0; m <= R; ++m) {
+            const T xl = beta_weight<T, R, NS>(tb, dp[kk], m, pfl);
+            const T xr = beta_weight<T, R, NS>(tb, dm[kk], m + 1, pfr);
+            T sl = tb.sl1[m] * fcp, sr = tb.sr1[m] * fcm;
+#pragma unroll
+            for (int j = 0; j <= R; ++j) {
+                if (m + j != R) sl = fma(tb.wl[m][j], dp[kk][m + j], sl);
+                if (1 + m + j != R) sr = fma(tb.wr[m][j], dm[kk][1 + m + j], sr);
+            }
+            const T yl = Num<T>::mul_rn(tb.gl[m], xl);
+            const T yr = Num<T>::mul_rn(tb.gr[m], xr);
+            numL = fma(yl, sl, numL);
+            denL = Num<T>::add_rn(denL, yl);
+            numR = fma(yr, sr, numR);
+            denR = Num<T>::add_rn(denR, yr);
+        }
+        dq[kk] = fma(numL, Num<T>::rcp(denL), numR * Num<T>::rcp(denR));
+    }
+
+    // back-projection A = (dU/dV) R_V dq at the Roe state
+    T w[NC];
+    w[0] = dq[0] + dq[1] + dq[E];
+    w[1] = f.cr * (dq[E] - dq[0]);
+#pragma unroll
+    for (int a = 2; a < E; ++a) w[a] = dq[a];
+    w[E] = f.c2 * (dq[0] + dq[E]);
+    A[0] = w[0];
+    T ke = T(0);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        A[1 + a] = fma(f.vel[a], w[0], f.rbar * w[1 + a]);
+        ke = fma(f.vel[a], w[1 + a], ke);
+    }
+    A[E] = fma(T(0.5) * f.q2, w[0], fma(f.rbar, ke, w[E] * f.igm1));
+    return ok;
+}
+
+// Scheme variants chosen at compile time: bit 0 the non-zero-mean smoothness
+// indicators, bit 1 the FD-Flux form.
+constexpr int kVarMean = 1, kVarFdFlux = 2;
+
+template <typename T, int NC, int R, int VAR>
+__device__ __forceinline__ bool face_eval(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
+                                          T (&B)[NC])
+{
+    if constexpr ((VAR & kVarFdFlux) != 0) return face_fdf<T, NC, R, (VAR & kVarMean) != 0>(st, tb, A, B);
+    else return face_rel<T, NC, R, (VAR & kVarMean) != 0>(st, tb, A, B);
+}
+
 // Weights of the corrected-flux difference: with the face-flux correction
 // f^_{s+1/2} = F + alpha D2F + beta D4F (Eqs. numFlux_cor, FD-ders; alpha = -1/24,
 // beta = 3/640), f^_{i+1/2} - f^_{i-1/2} = sum_{k=-2..2} c_k dF_{i+k} where
@@ -422,6 +610,16 @@ __device__ __forceinline__ T corrected_divergence(T d0, T d1, T d2, T d3, T d4)
     constexpr double al = -1.0 / 24.0, be = 3.0 / 640.0;
     const T c0 = T(be), c1 = T(al - 4.0 * be), c2 = T(1.0 - 2.0 * al + 6.0 * be);
     return fma(c0, d0 + d4, fma(c1, d1 + d3, c2 * d2));
+}
+
+// Flux difference across a cell from the five face-flux differences around it:
+// corrected in the FD-Prim form; in the FD-Flux form the reconstructed flux is
+// itself the numerical flux (Eq. design), so only the centre one is used.
+template <typename T, int VAR>
+__device__ __forceinline__ T flux_divergence(T d0, T d1, T d2, T d3, T d4)
+{
+    if constexpr ((VAR & kVarFdFlux) != 0) return d2;
+    else return corrected_divergence<T>(d0, d1, d2, d3, d4);
 }
 
 // Index of cell i along a dimension of n cells after the boundary map:

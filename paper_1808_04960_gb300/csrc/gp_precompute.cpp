@@ -18,6 +18,12 @@
 // 4 (a-b)^2.  So a single exponential is evaluated (Taylor series after
 // halving the argument, squared back) and every entry is an exact-integer
 // power of q, which keeps all entries accurate to a few units of 2^-104.
+//
+// Reconstruction tables (FD-Flux form, Section 2: the point fluxes are cell
+// averages of the function whose face values are wanted, Eqs. prim_F and
+// design) condition the GP on cell averages.  Their covariances are power
+// series in a = 1/(2 l^2) with exact-integer coefficients (see cavg_cov and
+// point_cell_cov), summed in double-double.
 #include "gp_precompute.h"
 
 #include <cmath>
@@ -144,6 +150,85 @@ dd se_entry(dd q, int a2, int b2)
     return pow_int(q, d * d);
 }
 
+// b^e for small integers (either sign), exact in double-double while below 2^106.
+dd ipow(int b, int e)
+{
+    dd r = make(1.0);
+    for (int k = 0; k < e; ++k) r = mul_d(r, (double)b);
+    return r;
+}
+
+// Covariance of the averages over two unit cells whose centres are delta apart
+// (units of dx) under exp(-a u^2):
+//   C(delta) = int_{-1}^{1} (1 - |t|) exp(-a (delta + t)^2) dt
+//            = sum_n (-a)^n / n! * [(delta+1)^(2n+2) - 2 delta^(2n+2) + (delta-1)^(2n+2)] / ((2n+1)(2n+2)),
+// the bracket being the second difference of the second antiderivative of u^(2n).
+dd cavg_cov(dd a, int delta)
+{
+    if (delta < 0) delta = -delta;
+    const double xmax = delta + 1.0;
+    dd coef = make(1.0), sum = make(0.0);
+    for (int n = 0; n < 400; ++n) {
+        if (n > 0) coef = div(mul(coef, neg(a)), make((double)n));
+        const int e = 2 * n + 2;
+        dd m = add(sub(ipow(delta + 1, e), mul_d(ipow(delta, e), 2.0)), ipow(delta - 1, e));
+        dd term = div(mul(coef, m), make((double)(2 * n + 1) * (double)(2 * n + 2)));
+        sum = add(sum, term);
+        if (n > a.hi * xmax * xmax + 4 && std::fabs(term.hi) < 1e-36 * std::fabs(sum.hi)) break;
+    }
+    return sum;
+}
+
+// Covariance of the point value at offset u = u2/2 (u2 odd, units of dx) from a cell
+// centre with the average over that unit cell:
+//   T(u) = int_{-1/2}^{1/2} exp(-a (u + t)^2) dt
+//        = sum_n (-a)^n / n! * [(u+1/2)^(2n+1) - (u-1/2)^(2n+1)] / (2n+1).
+dd point_cell_cov(dd a, int u2)
+{
+    const int hi = (u2 + 1) / 2, lo = (u2 - 1) / 2;   // u + 1/2 and u - 1/2, integers
+    const double xmax = std::fmax(std::fabs((double)hi), std::fabs((double)lo));
+    dd coef = make(1.0), sum = make(0.0);
+    for (int n = 0; n < 400; ++n) {
+        if (n > 0) coef = div(mul(coef, neg(a)), make((double)n));
+        const int e = 2 * n + 1;
+        dd term = div(mul(coef, sub(ipow(hi, e), ipow(lo, e))), make((double)(2 * n + 1)));
+        sum = add(sum, term);
+        if (n > a.hi * xmax * xmax + 4 && std::fabs(term.hi) < 1e-36 * std::fabs(sum.hi)) break;
+    }
+    return sum;
+}
+
+// Polynomial reconstruction at xs2/2 from averages over unit cells centred at
+// pts2[j]/2: the primitive function at the n+1 cell edges is interpolated and
+// differentiated, w_j = sum_{m>j} L'_m(x*) with L_m the Lagrange basis on the edges.
+void poly_recon_weights(const int *pts2, int n, int xs2, dd *w)
+{
+    int e2[kMaxBig + 1];                 // edges in half-units
+    e2[0] = pts2[0] - 1;
+    for (int j = 0; j < n; ++j) e2[j + 1] = pts2[j] + 1;
+    const int ne = n + 1;
+    dd dL[kMaxBig + 1];
+    for (int m = 0; m < ne; ++m) {
+        dd den = make(1.0);
+        for (int l = 0; l < ne; ++l)
+            if (l != m) den = mul_d(den, 0.5 * (e2[m] - e2[l]));
+        dd num = make(0.0);
+        for (int l = 0; l < ne; ++l) {
+            if (l == m) continue;
+            dd prod = make(1.0);
+            for (int q = 0; q < ne; ++q)
+                if (q != m && q != l) prod = mul_d(prod, 0.5 * (xs2 - e2[q]));
+            num = add(num, prod);
+        }
+        dL[m] = div(num, den);
+    }
+    for (int j = 0; j < n; ++j) {
+        dd s = make(0.0);
+        for (int m = j + 1; m < ne; ++m) s = add(s, dL[m]);
+        w[j] = s;
+    }
+}
+
 // Cholesky factorisation A = C C^T (lower C) and solves, n <= kMaxBig.
 struct Chol {
     int n;
@@ -209,20 +294,29 @@ void lagrange_weights(const int *pts2, int n, int xs2, dd *w)
     }
 }
 
-// GP weights for the points 2*p2[k] (half-units) and the prediction point xs2
-// (half-units): w = K^{-1} k*; with `poly`, Lagrange weights instead.
-bool gp_weights(dd q, const int *pts2, int n, int xs2, dd *w, double *cond, int poly = 0)
+// Prediction weights for the points 2*p2[k] (half-units) and the prediction
+// point xs2 (half-units).  Point data: GP weights w = K^{-1} k*, or with
+// `poly` Lagrange weights.  Cell-average data (`recon`, a = 1/(2 l^2)): GP
+// weights w = C^{-1} T, or with `poly` polynomial reconstruction weights.
+struct WeightKind {
+    int poly, recon;
+    dd a;
+};
+
+bool gp_weights(dd q, const int *pts2, int n, int xs2, dd *w, double *cond, const WeightKind &kind)
 {
-    if (poly) {
-        lagrange_weights(pts2, n, xs2, w);
+    if (kind.poly) {
+        if (kind.recon) poly_recon_weights(pts2, n, xs2, w);
+        else lagrange_weights(pts2, n, xs2, w);
         if (cond) *cond = 1.0;
         return true;
     }
     dd K[kMaxBig][kMaxBig];
     dd ks[kMaxBig];
     for (int a = 0; a < n; ++a) {
-        for (int b = 0; b < n; ++b) K[a][b] = se_entry(q, pts2[a], pts2[b]);
-        ks[a] = se_entry(q, xs2, pts2[a]);
+        for (int b = 0; b < n; ++b)
+            K[a][b] = kind.recon ? cavg_cov(kind.a, (pts2[a] - pts2[b]) / 2) : se_entry(q, pts2[a], pts2[b]);
+        ks[a] = kind.recon ? point_cell_cov(kind.a, xs2 - pts2[a]) : se_entry(q, xs2, pts2[a]);
     }
     Chol ch = cholesky(K, n);
     if (cond) *cond = ch.cond_est;
@@ -276,13 +370,13 @@ void jacobi(dd A[kMaxS][kMaxS], int n, dd V[kMaxS][kMaxS])
 // Linear weights for one prediction point: sub-stencil weights, full-stencil
 // weights, then least squares of M gamma = w through the normal equations.
 bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam, double *resid, double *cond,
-                 double *sum1, char *err, std::size_t errlen, int poly)
+                 double *sum1, char *err, std::size_t errlen, const WeightKind &kind)
 {
     const int S = R + 1, B = 2 * R + 1;
     int big2[kMaxBig];
     for (int j = 0; j < B; ++j) big2[j] = 2 * (j - R);
     dd wb[kMaxBig];
-    if (!gp_weights(q, big2, B, xs2, wb, cond, poly)) {
+    if (!gp_weights(q, big2, B, xs2, wb, cond, kind)) {
         std::snprintf(err, errlen, "covariance K of the %d-point stencil is not positive definite in double-double", B);
         return false;
     }
@@ -290,7 +384,7 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
     for (int m = 0; m < S; ++m) {
         int p2[kMaxS];
         for (int j = 0; j < S; ++j) p2[j] = 2 * (-R + m + j);
-        if (!gp_weights(q, p2, S, xs2, ws[m], nullptr, poly)) {
+        if (!gp_weights(q, p2, S, xs2, ws[m], nullptr, kind)) {
             std::snprintf(err, errlen, "sub-stencil covariance K_m is not positive definite in double-double");
             return false;
         }
@@ -339,7 +433,7 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
 
 }  // namespace
 
-int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std::size_t errlen, int poly)
+int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std::size_t errlen, int poly, int recon)
 {
     if (R < 1 || R > kMaxR) {
         std::snprintf(err, errlen, "R=%d out of range [1,%d]", R, kMaxR);
@@ -359,10 +453,14 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
     // q = exp(-1/(8 l^2)) in double-double; 1/(8 l^2) formed exactly enough by a dd division
     dd ql = exp_dd(neg(div(make(1.0), mul_d(mul(make(ell), make(ell)), 8.0))));
     dd qs = exp_dd(neg(div(make(1.0), mul_d(mul(make(sigma), make(sigma)), 8.0))));
+    WeightKind kind;
+    kind.poly = poly;
+    kind.recon = recon;
+    kind.a = div(make(0.5), mul(make(ell), make(ell)));
     double cond = 0.0, resid_r = 0.0;
-    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, out->sl1, err, errlen, poly))
+    if (!side_tables(ql, R, +1, out->wl, out->wbig_l, out->gl, &out->ls_residual, &cond, out->sl1, err, errlen, kind))
         return 2;
-    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen, poly))
+    if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen, kind))
         return 2;
     out->cond_estimate = cond;
     // double-double carries ~2^-104 relative; demand cond * 2^-104 < 1e-6

@@ -37,10 +37,11 @@ struct GpTables {
 
 // Returns 0 on success; otherwise writes a message to err and returns
 // 1 (bad argument) or 2 (ill-conditioned beyond double-double).
-// poly = 1: candidate and full-stencil weights are Lagrange (polynomial)
-// interpolation weights instead of GP weights (the WENO-GP hybrid); the linear
-// weights, K_m(sigma) and P are computed as usual.
+// poly = 1: candidate and full-stencil weights are polynomial instead of GP
+// weights (the WENO-GP hybrid); the linear weights, K_m(sigma) and P are
+// computed as usual.  recon = 1: the weights predict a point value from cell
+// averages (reconstruction, for the FD-Flux form) instead of from point values.
 int gp_precompute(int R, double ell_over_dx, double sigma_over_dx, GpTables *out, char *err, std::size_t errlen,
-                  int poly = 0);
+                  int poly = 0, int recon = 0);
 
 }  // namespace gpweno

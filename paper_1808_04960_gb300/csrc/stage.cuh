@@ -148,7 +148,7 @@ __device__ __forceinline__ void rates2d(const T (&u)[4], T gam, const T (&idx)[3
 
 // One segment: rows [y0, y1) of strip `strip` of the xy-plane starting at cell offset zoff.
 // NC = 4 (2D) or 5 (an xy-plane of a 3D grid).
-template <typename T, int R, int NT, int NC = 4, bool MEAN = false>
+template <typename T, int R, int NT, int NC = 4, int VAR = 0>
 __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, int strip, int y0,
                                                 int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok, long zoff = 0)
 {
@@ -224,7 +224,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 for (int c = 0; c < NC; ++c) st[q][c] = row[(c == 1 ? 2 : (c == 2 ? 1 : c)) * STRIDE];
             }
             T An[NC], Bn[NC];
-            ok = face_rel<T, NC, R, MEAN>(st, tb, An, Bn) && ok;
+            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
             T Ac[NC], Bc[NC];   // back to natural order
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -252,7 +252,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
 #pragma unroll
                 for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + q];
             T An[NC], Bn[NC];
-            ok = face_rel<T, NC, R, MEAN>(st, tb, An, Bn) && ok;
+            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 FA[c * NT + tid] = An[c];
@@ -272,8 +272,8 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 T dx[5];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
-                const T divx = corrected_divergence<T>(dx[0], dx[1], dx[2], dx[3], dx[4]);
-                const T divy = corrected_divergence<T>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
+                const T divx = flux_divergence<T, VAR>(dx[0], dx[1], dx[2], dx[3], dx[4]);
+                const T divy = flux_divergence<T, VAR>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
                 const T L = -fma(divx, idx[0], divy * idx[1]);
                 if (NC == 5 || a.mode == kModePartial) {
                     a.out[c * plane + cell] = L;
@@ -316,7 +316,7 @@ __device__ __forceinline__ void finish_block(const StageArgs<T> &a, T r0, T r1, 
     if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.flags, 1);
 }
 
-template <typename T, int R, int NT, bool MEAN = false>
+template <typename T, int R, int NT, int VAR = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
         const int strip = (int)(u / ny);
         const int y0 = (int)(u - (long long)strip * ny);
         const int y1 = (int)min((long long)ny, y0 + (uend - u));
-        stage2d_segment<T, R, NT, 4, MEAN>(a, tb, strip, y0, y1, smem, dt, rmx, rmy, ok);
+        stage2d_segment<T, R, NT, 4, VAR>(a, tb, strip, y0, y1, smem, dt, rmx, rmy, ok);
         u += y1 - y0;
     }
     finish_block<T>(a, rmx, rmy, T(0), ok);
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
 // -div_z/dz to P and applies the stage update.  P is a buffer the update later
 // overwrites cell by cell (each cell reads its own P first), so 3D needs no
 // scratch beyond 2D's.
-template <typename T, int R, int NT, bool MEAN = false>
+template <typename T, int R, int NT, int VAR = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(Sta
         const int strip = (int)(rem / ny);
         const int y0 = (int)(rem - (long)strip * ny);
         const int y1 = (int)min((long long)ny, y0 + (uend - u));
-        stage2d_segment<T, R, NT, 5, MEAN>(a, tb, strip, y0, y1, smem, T(0), rmx, rmy, ok, (long)z * nx * ny);
+        stage2d_segment<T, R, NT, 5, VAR>(a, tb, strip, y0, y1, smem, T(0), rmx, rmy, ok, (long)z * nx * ny);
         u += y1 - y0;
     }
     if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.flags, 1);
@@ -400,7 +400,7 @@ __device__ __forceinline__ void rates3d(const T (&u)[5], T gam, const T (&idx)[3
 }
 
 // z-marching over columns [c0, c0+NT) of the flattened xy-plane, planes [z0, z1).
-template <typename T, int R, int NT, bool MEAN = false>
+template <typename T, int R, int NT, int VAR = 0>
 __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, long c0, int z0,
                                                int z1, T *ring, T dt, T (&rm)[3], bool &ok)
 {
@@ -464,7 +464,7 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
                 st[q][4] = rowp[4 * NT];
             }
             T An[NC], Bn[NC];
-            ok = face_rel<T, NC, R, MEAN>(st, tb, An, Bn) && ok;
+            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
             const T Ac[NC] = {An[0], An[2], An[3], An[1], An[4]};
             const T Bc[NC] = {Bn[0], Bn[2], Bn[3], Bn[1], Bn[4]};
 #pragma unroll
@@ -483,7 +483,7 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
             T res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const T divz = corrected_divergence<T>(Dz[0][c], Dz[1][c], Dz[2][c], Dz[3][c], Dz[4][c]);
+                const T divz = flux_divergence<T, VAR>(Dz[0][c], Dz[1][c], Dz[2][c], Dz[3][c], Dz[4][c]);
                 const T L = fma(-divz, idx[2], pv[c]);
                 const T un = a.u0_is_stencil ? urow[c * NT] : u0[c];
                 res[c] = stage_epilogue<T>(a, c * cs + cell, L, un, din[c], lov[c], dt);
@@ -501,7 +501,7 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
     }
 }
 
-template <typename T, int R, int NT, bool MEAN = false>
+template <typename T, int R, int NT, int VAR = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(StageArgs<T> a, FaceTables<T, R> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(Stag
         const long g = (long)(u / nz);
         const int z0 = (int)(u - (long long)g * nz);
         const int z1 = (int)min((long long)nz, z0 + (uend - u));
-        stagez_segment<T, R, NT, MEAN>(a, tb, g * NT, z0, z1, ring, dt, rm, ok);
+        stagez_segment<T, R, NT, VAR>(a, tb, g * NT, z0, z1, ring, dt, rm, ok);
         u += z1 - z0;
     }
     finish_block<T>(a, rm[0], rm[1], rm[2], ok);
@@ -535,7 +535,7 @@ constexpr size_t stage1d_smem_bytes()
     return sizeof(T) * (size_t)(3 * (NT - 5 + 2 * (R + 3)) + 2 * 3 * NT);
 }
 
-template <typename T, int R, int NT, bool MEAN = false>
+template <typename T, int R, int NT, int VAR = 0>
 __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
 {
     constexpr int G = R + 3, NC = 3, NS = 2 * R + 2;
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<
 #pragma unroll
                 for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + tid + q];
             T An[NC], Bn[NC];
-            ok = face_rel<T, NC, R, MEAN>(st, tb, An, Bn) && ok;
+            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 FA[c * NT + tid] = An[c];
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<
                 T dx[5];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
-                const T L = -corrected_divergence<T>(dx[0], dx[1], dx[2], dx[3], dx[4]) * a.idx[0];
+                const T L = -flux_divergence<T, VAR>(dx[0], dx[1], dx[2], dx[3], dx[4]) * a.idx[0];
                 const long cell = (long)c * nx + x0 + tid;
                 const bool epi = a.mode != kModeRHS;
                 const T u0 = a.u0_is_stencil ? row[c * STRIDE + G + tid] : (epi ? a.U0[cell] : T(0));

@@ -8,8 +8,13 @@ namespace gpweno {
 
 gpweno_status launch_stage_f32(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    if (p->opts.beta_mean) return launch_stage_f32_mean(p, io, st);
-    return launch_stage_T<float, false>(p, io, st);
+    const int var = (p->opts.beta_mean ? kVarMean : 0) | (p->opts.scheme ? kVarFdFlux : 0);
+    switch (var) {
+    case kVarMean: return launch_stage_f32_var1(p, io, st);
+    case kVarFdFlux: return launch_stage_f32_var2(p, io, st);
+    case kVarFdFlux | kVarMean: return launch_stage_f32_var3(p, io, st);
+    default: return launch_stage_T<float, 0>(p, io, st);
+    }
 }
 
 gpweno_status launch_max_rate_f32(gpweno_plan p, const void *U, cudaStream_t st)

@@ -1,0 +1,14 @@
+// FP64 instantiations of the stage kernels for the FD-Flux form (reconstruction of the split point fluxes);
+// a translation unit of its own so that it compiles in parallel with the others.
+#include <cstring>
+
+#include "dispatch.cuh"
+
+namespace gpweno {
+
+gpweno_status launch_stage_f64_var2(gpweno_plan p, const StageIO &io, cudaStream_t st)
+{
+    return launch_stage_T<double, 2>(p, io, st);
+}
+
+}  // namespace gpweno

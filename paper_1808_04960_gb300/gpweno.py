@@ -36,7 +36,7 @@ class Dims(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("sigma_over_dx", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("cfl", ctypes.c_double), ("flux_form", ctypes.c_int),
-                ("beta_mean", ctypes.c_int), ("candidates", ctypes.c_int)]
+                ("beta_mean", ctypes.c_int), ("candidates", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -61,7 +61,7 @@ def load(path: str | None = None):
             "gpweno_plan_create": (i, [ctypes.POINTER(vp), i, d, ctypes.POINTER(Dims), d, ctypes.POINTER(Opts)]),
             "gpweno_plan_destroy": (i, [vp]),
             "gpweno_plan_tables": (i, [vp, dp, dp, dp, dp]),
-            "gpweno_gp_tables": (i, [i, d, d, i, dp, dp, dp, dp, dp, dp]),
+            "gpweno_gp_tables": (i, [i, d, d, i, i, dp, dp, dp, dp, dp, dp]),
             "gpweno_rhs": (i, [vp, vp, vp, vp]),
             "gpweno_rk3_step": (i, [vp, vp, vp, d, vp, vp]),
             "gpweno_cfl_dt": (i, [vp, vp, d, vp, vp]),
@@ -102,13 +102,15 @@ def _dbl(n):
     return (ctypes.c_double * n)()
 
 
-def gp_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, candidates: str = "gp") -> dict:
+def gp_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, candidates: str = "gp",
+              scheme: str = "fdprim") -> dict:
     """The library's double-double tables, computed on the host (no device needed)."""
     import numpy as np
     S = R + 1
     wm, g, P, wb, wmr, gr = _dbl(S * S), _dbl(S), _dbl(S * S), _dbl(2 * R + 1), _dbl(S * S), _dbl(S)
     _check(load().gpweno_gp_tables(int(R), float(ell_over_dx), float(sigma_over_dx),
-                                   {"gp": 0, "poly": 1}[candidates], wm, g, P, wb, wmr, gr), "gpweno_gp_tables")
+                                   {"gp": 0, "poly": 1}[candidates], {"fdprim": 0, "fdflux": 1}[scheme],
+                                   wm, g, P, wb, wmr, gr), "gpweno_gp_tables")
     a = lambda x, shape: np.array(list(x), dtype=np.float64).reshape(shape)
     return dict(w_sub=a(wm, (S, S)), gamma=a(g, (S,)), P=a(P, (S, S)), w_big=a(wb, (2 * R + 1,)),
                 w_sub_r=a(wmr, (S, S)), gamma_r=a(gr, (S,)))
@@ -134,7 +136,7 @@ class Plan:
     """
 
     def __init__(self, R, ell_over_dx, shape, dx, bc, gamma=1.4, sigma_over_dx=3.0, eps=1e-36, p=2,
-                 dtype="f32", cfl=0.0, flux="lf", beta_mean=False, candidates="gp"):
+                 dtype="f32", cfl=0.0, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim"):
         import torch
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
@@ -162,6 +164,7 @@ class Plan:
         opts.flux_form = {"lf": 0, "hllc": 1, "hll": 2}[flux]
         opts.beta_mean = 1 if beta_mean else 0
         opts.candidates = {"gp": 0, "poly": 1}[candidates]
+        opts.scheme = {"fdprim": 0, "fdflux": 1}[scheme]
         h = ctypes.c_void_p()
         _check(self.lib.gpweno_plan_create(ctypes.byref(h), self.R, float(ell_over_dx), ctypes.byref(dims),
                                            float(gamma), ctypes.byref(opts)), "gpweno_plan_create")

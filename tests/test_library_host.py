@@ -102,10 +102,14 @@ def test_dd_poly_tables_match_oracle(lib, R):
 
 
 def test_variant_options_checked(lib):
-    """beta_mean and candidates outside {0, 1} are refused by the C ABI before any device work."""
+    """beta_mean, candidates and scheme outside {0, 1}, and FD-Flux with a face solver, are refused
+    by the C ABI before any device work."""
     import ctypes
     with pytest.raises(gpweno.GpwenoError) as e:
-        gpweno._check(lib.gpweno_gp_tables(2, 12.0, 3.0, 2, None, None, None, None, None, None), "gp_tables")
+        gpweno._check(lib.gpweno_gp_tables(2, 12.0, 3.0, 2, 0, None, None, None, None, None, None), "gp_tables")
+    assert e.value.status == gpweno.ERR_ARG
+    with pytest.raises(gpweno.GpwenoError) as e:
+        gpweno._check(lib.gpweno_gp_tables(2, 12.0, 3.0, 0, 2, None, None, None, None, None, None), "gp_tables")
     assert e.value.status == gpweno.ERR_ARG
     dims = gpweno.Dims()
     dims.ndim = 2
@@ -113,10 +117,32 @@ def test_variant_options_checked(lib):
         dims.n[a] = 16 if a < 2 else 1
         dims.dx[a] = 0.1
         dims.bc_lo[a] = dims.bc_hi[a] = 0
-    for field in ("beta_mean", "candidates"):
+    for field, val in (("beta_mean", 3), ("candidates", 3), ("scheme", 2), ("flux_form", 3), ("scheme+flux", 1)):
         o = gpweno.Opts()
         lib.gpweno_default_opts(ctypes.byref(o))
-        setattr(o, field, 3)
+        if field == "scheme+flux":
+            o.scheme, o.flux_form = 1, 1
+        else:
+            setattr(o, field, val)
         h = ctypes.c_void_p()
         st = lib.gpweno_plan_create(ctypes.byref(h), 2, 12.0, ctypes.byref(dims), 1.4, ctypes.byref(o))
         assert st == gpweno.ERR_ARG and not h.value, field
+
+
+@pytest.mark.parametrize("R,ell", [(1, 12.0), (2, 12.0), (3, 12.0), (2, 4.0), (3, 24.0), (2, 1.5)])
+def test_dd_recon_tables_match_oracle(lib, R, ell):
+    """Reconstruction weights (FD-Flux): the library's power series of the cell-averaged kernel
+    in double-double against the oracle's 100-digit erf closed form."""
+    t = gpweno.gp_tables(R, ell, 3.0, scheme="fdflux")
+    ol = OT.tables(R, ell, 3.0, 0.5, recon=True)
+    orr = OT.tables(R, ell, 3.0, -0.5, recon=True)
+    tol = 1e-13
+    np.testing.assert_allclose(t["w_sub"], ol["w_sub"], rtol=0, atol=tol * np.abs(ol["w_sub"]).max())
+    np.testing.assert_allclose(t["w_big"], ol["w_big"], rtol=0, atol=tol * np.abs(ol["w_big"]).max())
+    np.testing.assert_allclose(t["gamma"], ol["gamma"], rtol=tol, atol=0)
+    np.testing.assert_allclose(t["w_sub_r"], orr["w_sub"], rtol=0, atol=tol * np.abs(orr["w_sub"]).max())
+    np.testing.assert_allclose(t["gamma_r"], orr["gamma"], rtol=tol, atol=0)
+    tp = gpweno.gp_tables(R, ell, 3.0, candidates="poly", scheme="fdflux")
+    op = OT.tables(R, ell, 3.0, 0.5, poly=True, recon=True)
+    np.testing.assert_allclose(tp["w_sub"], op["w_sub"], rtol=0, atol=1e-15 * np.abs(op["w_sub"]).max())
+    np.testing.assert_allclose(tp["gamma"], op["gamma"], rtol=1e-14, atol=0)
