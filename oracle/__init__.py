@@ -24,10 +24,15 @@ Parity status per function (pins are in ``tests/test_oracle_*.py``):
                             free stream, conservation, mirror symmetry, order 2R+1
                             with reconstruction weights and 2 with point weights,
                             Eq. flux_2nd)
+  GP-AO (gp_ao)             pinned (equal weights give the high-order GP
+                            prediction; coefficients sum to one; smooth small
+                            stencils win at a jump; scheme invariants; measured
+                            smooth order ~3.4, below the paper's 2R+1 claim)
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -61,7 +66,9 @@ class _Cfg(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("wl", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("wr", ctypes.c_void_p),
                 ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int),
-                ("beta_mean", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("beta_mean", ctypes.c_int), ("scheme", ctypes.c_int), ("ao", ctypes.c_int),
+                ("ao_gamma_hi", ctypes.c_double), ("ao_gamma_lo", ctypes.c_double), ("ao_l", ctypes.c_void_p),
+                ("ao_r", ctypes.c_void_p), ("ao_kinv", ctypes.c_void_p), ("ao_const", ctypes.c_double * 3)]
 
 
 def _load():
@@ -108,11 +115,14 @@ class Oracle:
 
     def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
                  gamma=1.4, eps=1e-36, p=2, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim",
-                 recon_weights=None):
+                 recon_weights=None, ao=False, ao_gamma_hi=0.85, ao_gamma_lo=0.85, ao_beta="datafit"):
         """scheme "fdprim": GP-WENO Riemann states, face flux, high-order correction (Section 2,
         Del Zanna's form); "fdflux": reconstruction of the split point fluxes (Section 2,
         Shu-Osher's form) with reconstruction weights unless recon_weights=False (the naive
-        point-value weights of Eq. flux_2nd, kept for the order test)."""
+        point-value weights of Eq. flux_2nd, kept for the order test).
+        ao: GP-AO of Appendix A instead of GP-WENO (R = 2: AO(2,3); R = 3: AO(3,2,3)), with
+        beta the data-fit term of Eq. log-like ("datafit") or the whole negative log-likelihood
+        with Sigma = 1 ("loglik")."""
         self.lib = _load()
         shape = tuple(int(s) for s in shape)
         self.ndim = len(shape)
@@ -141,6 +151,22 @@ class Oracle:
         c.flux = {"lf": 0, "hllc": 1, "hll": 2}[flux]
         c.beta_mean = 1 if beta_mean else 0
         c.scheme = {"fdprim": 0, "fdflux": 1}[scheme]
+        c.ao = 1 if ao else 0
+        if ao:
+            if scheme != "fdprim" or candidates != "gp":
+                raise ValueError("GP-AO is built on the FD-Prim scheme with GP candidates")
+            tl = gp_tables.ao_tables(R, ell_over_dx, sigma_over_dx, 0.5)
+            tr = gp_tables.ao_tables(R, ell_over_dx, sigma_over_dx, -0.5)
+            keys = ["hi", "lo", "3"] if R == 3 else ["hi", "3"]
+            side = lambda t: np.concatenate([t["w_" + k].ravel() for k in keys])
+            kinv = np.concatenate([tl["Kinv_" + k].ravel() for k in keys])
+            self._keep += [np.ascontiguousarray(side(tl)), np.ascontiguousarray(side(tr)),
+                           np.ascontiguousarray(kinv)]
+            c.ao_l, c.ao_r, c.ao_kinv = [a.ctypes.data for a in self._keep[-3:]]
+            c.ao_gamma_hi, c.ao_gamma_lo = float(ao_gamma_hi), float(ao_gamma_lo)
+            for i, (k, n) in enumerate((("hi", 2 * R + 1), ("lo", 2 * R - 1), ("3", 3))):
+                if ao_beta == "loglik" and ("logdet_" + k) in tl:
+                    c.ao_const[i] = 0.5 * n * math.log(2 * math.pi) + 0.5 * tl["logdet_" + k]
         self.cfg = c
         self.R = int(R)
         self.gamma = float(gamma)

@@ -62,6 +62,12 @@ typedef struct {
     int flux;          /* 0 = local Lax-Friedrichs, 1 = HLLC, 2 = HLL */
     int beta_mean;     /* 0 = zero-mean GP smoothness indicators (the paper's choice), 1 = mean f_centre */
     int scheme;        /* 0 = FD-Prim (Riemann states + face flux + correction), 1 = FD-Flux (Section 2) */
+    int ao;            /* 0 = GP-WENO; 1 = GP-AO (Appendix A): R = 2 gives AO(2,3), R = 3 gives AO(3,2,3) */
+    double ao_gamma_hi, ao_gamma_lo;
+    const double *ao_l;   /* x* = +1/2: w_hi[2R+1], w_lo[2R-1] (R = 3 only), w_3[3][3] */
+    const double *ao_r;   /* the same at x* = -1/2 */
+    const double *ao_kinv;/* K^-1 built with sigma: hi [(2R+1)^2], lo [(2R-1)^2] (R = 3 only), 3-point [9] */
+    double ao_const[3];   /* constant terms added to beta of the hi, lo and 3-point stencils */
 } oracle_cfg;
 
 static long ncells(const oracle_cfg *c) { return (long)c->n[0] * c->n[1] * c->n[2]; }
@@ -202,6 +208,66 @@ static double gp_weno(const oracle_cfg *c, const double *f, const double *w, con
     return out;
 }
 
+/* beta of one stencil for GP-AO: the data-fit term of the negative log-likelihood,
+ * (1/2) f^T K^-1 f (Eq. log-like; f relative to the centre value with beta_mean),
+ * plus the configured constant (the normalisation and complexity terms). */
+static double ao_beta(const oracle_cfg *c, const double *Kinv, const double *f, int n, double mean, double cst)
+{
+    double b = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int d = 0; d < n; ++d) b += (f[a] - mean) * Kinv[a * n + d] * (f[d] - mean);
+    return 0.5 * b + cst;
+}
+
+/* GP-AO(R,3) (Eq. GP-AO): the high-order prediction qh with its beta bh hybridised with the
+ * three 3-point predictions q3 and betas b3.  Nonlinear weights Eq. nonlin-AO with
+ * gamma_HI for the high-order stencil and gamma_m (Eq. CWENO-lin) for the small ones. */
+static double ao_r3(const oracle_cfg *c, double qh, double bh, const double *q3, const double *b3)
+{
+    double ghi = c->ao_gamma_hi, glo = c->ao_gamma_lo;
+    double g[3] = { 0.5 * (1.0 - ghi) * (1.0 - glo), (1.0 - ghi) * glo, 0.5 * (1.0 - ghi) * (1.0 - glo) };
+    double wh = ghi / pow(c->eps + bh, (double)c->p), w[3], sum = wh;
+    for (int m = 0; m < 3; ++m) {
+        w[m] = g[m] / pow(c->eps + b3[m], (double)c->p);
+        sum += w[m];
+    }
+    double oh = wh / sum;
+    double q = oh / ghi * qh;
+    for (int m = 0; m < 3; ++m) q += (w[m] / sum - oh / ghi * g[m]) * q3[m];
+    return q;
+}
+
+/* GP-AO prediction at one face centre from the 2R+1 values f[0..2R] centred on the
+ * stencil's cell (Appendix A): R = 2 gives AO(2,3); R = 3 gives the recursive
+ * AO(3,2,3) of Eqs. recursive-weights and AO-recursive. */
+static double gp_ao(const oracle_cfg *c, const double *f, const double *tab)
+{
+    int R = c->R, nh = 2 * R + 1, nl = R == 3 ? 2 * R - 1 : 0;
+    const double *w_hi = tab, *w_lo = tab + nh, *w3 = w_lo + nl;
+    const double *K_hi = c->ao_kinv, *K_lo = K_hi + nh * nh, *K3 = K_lo + nl * nl;
+    double mean = c->beta_mean ? f[R] : 0.0;
+    double q3[3], b3[3];
+    for (int m = 0; m < 3; ++m) {
+        const double *fm = f + R - 2 + m;     /* Eq. cweno_stencil: cells i-2..i, i-1..i+1, i..i+2 */
+        q3[m] = 0.0;
+        for (int j = 0; j < 3; ++j) q3[m] += w3[m * 3 + j] * fm[j];
+        b3[m] = ao_beta(c, K3, fm, 3, mean, c->ao_const[2]);
+    }
+    double qh = 0.0;
+    for (int j = 0; j < nh; ++j) qh += w_hi[j] * f[j];
+    double bh = ao_beta(c, K_hi, f, nh, mean, c->ao_const[0]);
+    double q_hi = ao_r3(c, qh, bh, q3, b3);
+    if (R == 2) return q_hi;
+    double ql = 0.0;
+    for (int j = 0; j < nl; ++j) ql += w_lo[j] * f[1 + j];
+    double bl = ao_beta(c, K_lo, f + 1, nl, mean, c->ao_const[1]);
+    double q_lo = ao_r3(c, ql, bl, q3, b3);
+    double ghi = c->ao_gamma_hi;
+    double vh = ghi / pow(c->eps + bh, (double)c->p), vl = (1.0 - ghi) / pow(c->eps + bl, (double)c->p);
+    double nuh = vh / (vh + vl), nul = vl / (vh + vl);
+    return nuh / ghi * q_hi + (nul - nuh / ghi * (1.0 - ghi)) * q_lo;
+}
+
 /* HLLC flux (Toro's three-wave approximate Riemann solver) of two conserved
  * normal-first states, with the wave speeds of Einfeldt from the Roe average:
  * S_L = min(u_L - c_L, u_roe - c_roe), S_R = max(u_R + c_R, u_roe + c_roe),
@@ -308,8 +374,9 @@ static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const i
     }
     double wL[OR_MAXC], wR[OR_MAXC];
     for (int f = 0; f < nc; ++f) {
-        wL[f] = gp_weno(c, &ch[f][0], c->wl, c->gl);   /* cells s-R..s+R, x* = +1/2 */
-        wR[f] = gp_weno(c, &ch[f][1], c->wr, c->gr);   /* cells s+1-R..s+1+R, x* = -1/2 */
+        /* cells s-R..s+R at x* = +1/2; cells s+1-R..s+1+R at x* = -1/2 */
+        wL[f] = c->ao ? gp_ao(c, &ch[f][0], c->ao_l) : gp_weno(c, &ch[f][0], c->wl, c->gl);
+        wR[f] = c->ao ? gp_ao(c, &ch[f][1], c->ao_r) : gp_weno(c, &ch[f][1], c->wr, c->gr);
     }
     double vL[OR_MAXC], vR[OR_MAXC], uL[OR_MAXC], uR[OR_MAXC];
     for (int a = 0; a < nc; ++a) {
@@ -441,7 +508,8 @@ static int face_flux_fd(const oracle_cfg *c, const double *U, int d, int s, cons
     }
     double hat[OR_MAXC];
     for (int f = 0; f < nc; ++f)
-        hat[f] = gp_weno(c, &gp[f][0], c->wl, c->gl) + gp_weno(c, &gm[f][1], c->wr, c->gr);
+        hat[f] = c->ao ? gp_ao(c, &gp[f][0], c->ao_l) + gp_ao(c, &gm[f][1], c->ao_r)
+                       : gp_weno(c, &gp[f][0], c->wl, c->gl) + gp_weno(c, &gm[f][1], c->wr, c->gr);
     for (int a = 0; a < nc; ++a) {
         double acc = 0.0;
         for (int f = 0; f < nc; ++f) acc += Rc[a][f] * hat[f];
@@ -595,5 +663,6 @@ int oracle_roe(int nc, double g, const double *uL, const double *uR, double *roe
 /* GP-WENO prediction exposed for unit tests: f has 2R+1 values. */
 double oracle_gp_weno(const oracle_cfg *c, const double *f, int right)
 {
+    if (c->ao) return gp_ao(c, f, right ? c->ao_r : c->ao_l);
     return right ? gp_weno(c, f, c->wr, c->gr) : gp_weno(c, f, c->wl, c->gl);
 }

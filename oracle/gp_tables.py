@@ -345,3 +345,36 @@ def scheme_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, poly: 
     tr = tables(R, ell_over_dx, sigma_over_dx, -0.5, poly, recon)
     return dict(R=int(R), wl=tl["w_sub"], gl=tl["gamma"], wr=tr["w_sub"], gr=tr["gamma"],
                 Kinv=tl["Kinv_sigma"], w_big_l=tl["w_big"], w_big_r=tr["w_big"])
+
+
+@lru_cache(maxsize=None)
+def _ao_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str):
+    ell, sigma, xs = Decimal(ell_s), Decimal(sigma_s), Decimal(xs_s)
+    out = {}
+    sizes = {"hi": R, "lo": R - 1, "3": 1}
+    for key, r in sizes.items():
+        pts = [Decimal(j) for j in range(-r, r + 1)]
+        out["w_" + key] = gp_weights(pts, xs, ell) if key != "3" else None
+        Ks = covariance(pts, sigma)
+        out["Kinv_" + key] = inverse(Ks)
+        lam, _ = jacobi_eigen(Ks)
+        with decimal.localcontext(_ctx()):
+            out["logdet_" + key] = sum((l.ln() for l in lam), Decimal(0))
+    # the three 3-point stencils of Eq. cweno_stencil: cells -2..0, -1..1, 0..2
+    out["w_3"] = [gp_weights([Decimal(j) for j in range(m - 2, m + 1)], xs, ell) for m in range(3)]
+    return out
+
+
+def ao_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, xstar: float = 0.5) -> dict:
+    """Tables of GP-AO (Appendix A) for one prediction point: GP weights of the high-order
+    stencil S_R (2R+1 points, Eq. q-intrp), of S_{R-1} (used by the recursive AO(R, R-1, 3)),
+    of the three 3-point stencils of Eq. cweno_stencil, and for each stencil size N the inverse
+    and log-determinant of K_N built with sigma (the terms of the log-likelihood, Eq. log-like)."""
+    assert R in (2, 3)
+    t = _ao_decimal(int(R), str(_D(ell_over_dx)), str(_D(sigma_over_dx)), str(_D(xstar)))
+    out = {}
+    for k, v in t.items():
+        if v is None:
+            continue
+        out[k] = float(v) if isinstance(v, Decimal) else _f64(v)
+    return out
