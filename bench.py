@@ -259,6 +259,7 @@ def run_gpu(args):
 
     batch = run_batch(args, stream) if args.batch_count > 0 else None
     extra = run_configs(args, stream) if args.configs else None
+    variants = run_variants(args, stream) if args.variant_steps > 0 else None
 
     if rank != 0:
         return None
@@ -295,6 +296,7 @@ def run_gpu(args):
         "e2e": e2e,
         "batch": batch,
         "configs": extra,
+        "variants": variants,
         "gpu_launches": r32["launches_per_step"] * args.steps,
         "clocks": r32["clocks"],
     }
@@ -427,6 +429,40 @@ def run_configs(args, stream):
     return out
 
 
+def run_variants(args, stream):
+    """Throughput of the scheme variants on one workload: the seeded four-quadrant Riemann
+    problem (GP-R2, l=12dx, CFL 0.4 from the device each step, FP32), the default scheme
+    (FD-Prim, Lax-Friedrichs face flux) beside HLLC, HLL, the non-zero-mean smoothness
+    indicators, the polynomial-candidate hybrid, the FD-Flux form and GP-AO(2,3); each with its
+    own algorithmic operation count for the ALU fraction."""
+    import torch
+
+    from paper_1808_04960_gb300 import costmodel, gpweno, workloads
+    n = args.variant_grid
+    U0, m = workloads.four_quadrant(n, seed=3)
+    cases = [("fdprim_lf", {}, {}), ("fdprim_hllc", {"flux": "hllc"}, {"flux": "hllc"}),
+             ("fdprim_hll", {"flux": "hll"}, {"flux": "hll"}),
+             ("fdprim_lf_beta_mean", {"beta_mean": True}, {"beta_mean": True}),
+             ("fdprim_lf_poly_candidates", {"candidates": "poly"}, {}),
+             ("fdflux", {"scheme": "fdflux"}, {"scheme": "fdflux"}),
+             ("ao_2_3", {"ao": True}, {"ao": True})]
+    out = {"workload": f"four-quadrant Riemann problem {n}x{n} on [0,1]^2, seeded states, outflow, GP-R2, "
+                       f"l=12dx, sigma=3dx, SSP-RK3, CFL 0.4 (device dt), FP32, {args.variant_steps} steps each"}
+    base = None
+    for name, opts, cm in cases:
+        plan = gpweno.Plan(2, 12.0, U0.shape[1:], m["dx"], m["bc"], dtype="f32", cfl=0.4, **opts)
+        U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+        flops = costmodel.flops_per_cell_stage(2, 2, **cm)
+        r = timed_cfl_run(plan, U, args.variant_steps, stream, flops, n * n, hbm_bytes_per_cell_stage(4, 4))
+        r["flops_per_cell_stage"] = flops
+        base = base or r["value"]
+        r["vs_default"] = r["value"] / base
+        out[name] = r
+        del U, plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(args, dt_full, gpu_compare=True):
     """The FP64 oracle, as it stands, on a bounded sample: the vortex at `--cpu-grid`^2 for
     `--cpu-steps` RK3 steps (single-threaded C).  Also reports the GPU FP32/FP64 error
@@ -522,6 +558,8 @@ def main():
     ap.add_argument("--fq-steps", type=int, default=100)
     ap.add_argument("--shock-grid", type=int, default=512)
     ap.add_argument("--shock-steps", type=int, default=20)
+    ap.add_argument("--variant-grid", type=int, default=2048, help="grid of the scheme-variant comparison")
+    ap.add_argument("--variant-steps", type=int, default=30, help="steps per variant (0: skip the comparison)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

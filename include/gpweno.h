@@ -96,7 +96,18 @@ typedef struct {
  *                  largest |u_n| + c over the face's 2R+2 stencil cells, projected
  *                  on the characteristic fields of the conservative Jacobian at
  *                  the Roe average, and reconstructed with GP weights conditioned
- *                  on cell averages; no correction.  Requires flux_form = 0. */
+ *                  on cell averages; no correction.  Requires flux_form = 0.
+ *   ao             1 = GP-AO (Appendix A) in place of GP-WENO for the Riemann
+ *                  states: R = 2 gives AO(2,3), R = 3 the recursive AO(3,2,3);
+ *                  the high-order GP prediction (Eq. q-intrp) hybridised with
+ *                  the GP-CWENO combination of the three 3-point stencils
+ *                  (Eqs. cweno_stencil, nonlin-AO, CWENO-lin, GP-AO,
+ *                  recursive-weights, AO-recursive), beta of each stencil the
+ *                  data-fit term (1/2) f^T K_N(sigma)^-1 f of Eq. log-like.
+ *                  Requires scheme = 0 and candidates = 0.
+ *   ao_gamma_hi, ao_gamma_lo
+ *                  gamma_HI and gamma_LO of Eq. CWENO-lin, in (0,1)
+ *                  (default 0.85 each). */
 typedef struct {
     double sigma_over_dx;
     double eps;
@@ -107,6 +118,9 @@ typedef struct {
     int beta_mean;
     int candidates;
     int scheme;
+    int ao;
+    double ao_gamma_hi;
+    double ao_gamma_lo;
 } gpweno_opts;
 
 void gpweno_default_opts(gpweno_opts *opts);
@@ -190,6 +204,16 @@ gpweno_status gpweno_rk3_step_noalloc(gpweno_plan plan, void *U, double dt, void
 /* *dt_dev (device double) = cfl / sum_d max over cells of (|u_d| + c)/dx_d. */
 gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *dt_dev, void *stream);
 
+/* Host-only: the double-double GP-AO tables of a plan with ao = 1 (for
+ * checking the precompute without a device).  w_hi: 2 x (2R+1) weights of the
+ * full stencil, left (x* = +1/2) then right (x* = -1/2); w_lo: 2 x (2R-1)
+ * weights of S_{R-1} (R = 3 only); w3: 2 x 3 x 3 weights of the 3-point
+ * stencils of Eq. cweno_stencil; P_hi, P_lo, P_3: the N x N factors
+ * v_h / sqrt(lambda_h) of K_N(sigma) (lambda ascending) for N = 2R+1, 2R-1, 3.
+ * Any pointer may be NULL.  Errors as gpweno_plan_create (R must be 2 or 3). */
+gpweno_status gpweno_ao_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_hi, double *w_lo,
+                               double *w3, double *P_hi, double *P_lo, double *P_3);
+
 /* Read and clear the plan's sticky non-physical flag (synchronises the
  * device).  *nonphysical = 1 if any kernel since the last read met rho <= 0,
  * p <= 0 or a NaN; returns GPWENO_ERR_CUDA if an earlier launch failed. */
@@ -198,9 +222,9 @@ gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 /* Batched 2D stepping (same per-face scheme as gpweno_rk3_step): one
  * persistent launch per RK stage serves n independent 2D plans of possibly
  * different grid size, R, l/dx, sigma, face flux, candidates and boundary
- * conditions (all plans must share dtype and device and use beta_mean = 0
- * and scheme = 0, else GPWENO_ERR_ARG; at most 12 distinct table sets per
- * radius).  The host cuts every
+ * conditions (all plans must share dtype and device and use beta_mean = 0,
+ * scheme = 0 and ao = 0, else GPWENO_ERR_ARG; at most 12 distinct table sets
+ * per radius).  The host cuts every
  * instance into strips and row segments and hands each CTA a contiguous run of
  * segments of equal estimated cost.  The batch refers to the member plans,
  * which must outlive it.  tune_cache: NULL, or the path of a text file of

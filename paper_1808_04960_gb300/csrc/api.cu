@@ -65,6 +65,9 @@ void gpweno_default_opts(gpweno_opts *o)
     o->beta_mean = 0;
     o->candidates = 0;
     o->scheme = 0;
+    o->ao = 0;
+    o->ao_gamma_hi = 0.85;
+    o->ao_gamma_lo = 0.85;
 }
 
 const char *gpweno_last_error(void) { return g_err; }
@@ -104,6 +107,19 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     }
     if ((o.beta_mean != 0 && o.beta_mean != 1) || (o.candidates != 0 && o.candidates != 1)) {
         set_error("beta_mean=%d and candidates=%d must each be 0 or 1", o.beta_mean, o.candidates);
+        return GPWENO_ERR_ARG;
+    }
+    if (o.ao != 0 && o.ao != 1) {
+        set_error("ao=%d must be 0 or 1", o.ao);
+        return GPWENO_ERR_ARG;
+    }
+    if (o.ao && ((R != 2 && R != 3) || o.scheme != 0 || o.candidates != 0)) {
+        set_error("GP-AO needs R = 2 or 3, scheme = 0 and candidates = 0 (R=%d, scheme=%d, candidates=%d)", R,
+                  o.scheme, o.candidates);
+        return GPWENO_ERR_ARG;
+    }
+    if (o.ao && !(o.ao_gamma_hi > 0.0 && o.ao_gamma_hi < 1.0 && o.ao_gamma_lo > 0.0 && o.ao_gamma_lo < 1.0)) {
+        set_error("ao_gamma_hi=%g and ao_gamma_lo=%g must lie in (0,1)", o.ao_gamma_hi, o.ao_gamma_lo);
         return GPWENO_ERR_ARG;
     }
     if (o.scheme != 0 && o.scheme != 1) {
@@ -161,6 +177,7 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
     p->ncell = ncell;
     char err[256];
     int rc = gp_precompute(R, ell_over_dx, o.sigma_over_dx, &p->tab, err, sizeof(err), o.candidates, o.scheme);
+    if (!rc && o.ao) rc = ao_precompute(R, ell_over_dx, o.sigma_over_dx, &p->ao, err, sizeof(err));
     if (rc) {
         set_error("%s", err);
         delete p;
@@ -226,6 +243,37 @@ gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, 
     if (w_big) std::memcpy(w_big, t.wbig_l, sizeof(double) * (2 * R + 1));
     if (w_m_r) std::memcpy(w_m_r, t.wr, sizeof(double) * S * S);
     if (gam_r) std::memcpy(gam_r, t.gr, sizeof(double) * S);
+    return GPWENO_OK;
+}
+
+gpweno_status gpweno_ao_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_hi, double *w_lo,
+                               double *w3, double *P_hi, double *P_lo, double *P_3)
+{
+    AoTables t;
+    char err[256];
+    GpTables g;
+    int rc = gp_precompute(R, ell_over_dx, sigma_over_dx, &g, err, sizeof(err));
+    if (!rc) rc = ao_precompute(R, ell_over_dx, sigma_over_dx, &t, err, sizeof(err));
+    if (rc) {
+        set_error("%s", err);
+        return rc == 1 ? GPWENO_ERR_ARG : GPWENO_ERR_PRECOMPUTE;
+    }
+    const int nh = 2 * R + 1, nl = 2 * R - 1;
+    if (w_hi) {
+        std::memcpy(w_hi, t.w_hi_l, sizeof(double) * nh);
+        std::memcpy(w_hi + nh, t.w_hi_r, sizeof(double) * nh);
+    }
+    if (w_lo && R == 3) {
+        std::memcpy(w_lo, t.w_lo_l, sizeof(double) * nl);
+        std::memcpy(w_lo + nl, t.w_lo_r, sizeof(double) * nl);
+    }
+    if (w3) {
+        std::memcpy(w3, t.w3_l, sizeof(double) * 9);
+        std::memcpy(w3 + 9, t.w3_r, sizeof(double) * 9);
+    }
+    if (P_hi) std::memcpy(P_hi, t.P_hi, sizeof(double) * nh * nh);
+    if (P_lo && R == 3) std::memcpy(P_lo, t.P_lo, sizeof(double) * nl * nl);
+    if (P_3) std::memcpy(P_3, t.P_3, sizeof(double) * 9);
     return GPWENO_OK;
 }
 
@@ -375,8 +423,8 @@ gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int 
             set_error("gpweno_plan_batch: plan %d is not a 2D single-grid plan", k);
             return GPWENO_ERR_ARG;
         }
-        if (p->opts.beta_mean || p->opts.scheme) {
-            set_error("gpweno_plan_batch: plan %d uses beta_mean = 1 or scheme = 1, which batches do not support", k);
+        if (p->opts.beta_mean || p->opts.scheme || p->opts.ao) {
+            set_error("gpweno_plan_batch: plan %d uses beta_mean, scheme = 1 or ao, which batches do not support", k);
             return GPWENO_ERR_ARG;
         }
         if (p->opts.dtype != plans[0]->opts.dtype || p->device != plans[0]->device) {

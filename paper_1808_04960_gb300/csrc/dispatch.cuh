@@ -37,6 +37,63 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
     return t;
 }
 
+// Tables of a scheme variant: GP-AO adds its own on top of the GP-WENO ones.
+template <typename T, int R, int VAR>
+TablesFor<T, R, VAR> make_tables_var(const gpweno_plan_s *p)
+{
+    if constexpr ((VAR & kVarAo) != 0) {
+        using AT = AoFaceTables<T, R>;
+        constexpr int NH = AT::NH, NL = AT::NL;
+        AT t;
+        std::memset(&t, 0, sizeof(t));
+        static_cast<FaceTables<T, R> &>(t) = make_tables<T, R>(p);
+        const AoTables &a = p->ao;
+        for (int j = 0; j < NH; ++j) {
+            t.whl[j] = (T)a.w_hi_l[j];
+            t.whr[j] = (T)a.w_hi_r[j];
+        }
+        t.shl = (T)a.s_hi_l;
+        t.shr = (T)a.s_hi_r;
+        if (R == 3) {
+            for (int j = 0; j < NL; ++j) {
+                t.wll[j] = (T)a.w_lo_l[j];
+                t.wlr[j] = (T)a.w_lo_r[j];
+            }
+            t.sll = (T)a.s_lo_l;
+            t.slr = (T)a.s_lo_r;
+            for (int k = 0; k < NL; ++k) {
+                for (int j = 0; j < (NL + 1) / 2; ++j) t.Plo[k][j] = (T)a.Ph_lo[k * NL + j];
+                t.Psum_lo[k] = (T)a.Psum_lo[k];
+            }
+        }
+        for (int m = 0; m < 3; ++m) {
+            for (int j = 0; j < 3; ++j) {
+                t.w3l[m][j] = (T)a.w3_l[3 * m + j];
+                t.w3r[m][j] = (T)a.w3_r[3 * m + j];
+            }
+            t.s3l[m] = (T)a.s3_l[m];
+            t.s3r[m] = (T)a.s3_r[m];
+        }
+        for (int k = 0; k < NH; ++k) {
+            for (int j = 0; j < (NH + 1) / 2; ++j) t.Phi[k][j] = (T)a.Ph_hi[k * NH + j];
+            t.Psum_hi[k] = (T)a.Psum_hi[k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            for (int j = 0; j < 2; ++j) t.P3[k][j] = (T)a.Ph_3[k * 3 + j];
+            t.Psum3[k] = (T)a.Psum_3[k];
+        }
+        const double gh = p->opts.ao_gamma_hi, gl = p->opts.ao_gamma_lo;
+        t.g_hi = (T)gh;
+        t.g_hi1 = (T)(1.0 - gh);
+        t.ig_hi = (T)(1.0 / gh);
+        t.g3[0] = t.g3[2] = (T)(0.5 * (1.0 - gh) * (1.0 - gl));
+        t.g3[1] = (T)((1.0 - gh) * gl);
+        return t;
+    } else {
+        return make_tables<T, R>(p);
+    }
+}
+
 // Schedule of the 2D kernel: strips as wide as the block allows (balanced
 // widths), one CTA per resident slot, each CTA an equal share of the strips'
 // rows (at least 8 rows, so the 5 warm-up y-face rows stay a minor cost).
@@ -76,7 +133,7 @@ template <typename T, int R, int VAR>
 gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t st)
 {
     StageArgs<T> a = a0;
-    const FaceTables<T, R> tb = make_tables<T, R>(p);
+    const TablesFor<T, R, VAR> tb = make_tables_var<T, R, VAR>(p);
     if (p->dims.ndim == 3) {
         constexpr int NT = kNT2D;
         // (1) xy-plane kernel: P = -(div_x/dx + div_y/dy)
@@ -175,7 +232,13 @@ gpweno_status launch_stage_T(gpweno_plan p, const StageIO &io, cudaStream_t st)
     a.dt_dev = io.dt_dev;
     a.rate = io.want_rate ? p->ws : nullptr;
     switch (p->R) {
-    case 1: return launch_stage_R<T, 1, VAR>(p, a, st);
+    case 1:
+        if constexpr ((VAR & kVarAo) != 0) {
+            set_error("GP-AO needs R = 2 or 3");
+            return GPWENO_ERR_ARG;
+        } else {
+            return launch_stage_R<T, 1, VAR>(p, a, st);
+        }
     case 2: return launch_stage_R<T, 2, VAR>(p, a, st);
     case 3: return launch_stage_R<T, 3, VAR>(p, a, st);
     default: set_error("R=%d not compiled", p->R); return GPWENO_ERR_ARG;

@@ -26,6 +26,7 @@
 // affected window holds data below ~1e-9, i.e. below FP32 resolution of the
 // state.  FP64 uses eps = 1e-36 exactly.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace gpweno {
@@ -278,6 +279,146 @@ __device__ __forceinline__ T beta_weight(const FaceTables<T, R> &tb, const T (&d
     return tb.p == 2 ? Num<T>::mul_rn(x, x) : x;
 }
 
+// GP-AO tables (Appendix A) on top of the GP-WENO ones: R = 2 serves AO(2,3),
+// R = 3 the recursive AO(3,2,3).  Weights of the full stencil S_R (hi), of
+// S_{R-1} (lo, R = 3), of the three 3-point stencils of Eq. cweno_stencil, for
+// the left (x* = +1/2) and right (x* = -1/2) states, with their sums minus
+// one; half-form factors of K_N(sigma) for N = 2R+1, 2R-1, 3; the linear
+// weights of Eq. CWENO-lin.
+template <typename T, int R>
+struct AoFaceTables : FaceTables<T, R> {
+    static constexpr int NH = 2 * R + 1, NL = R > 2 ? 2 * R - 1 : 1;
+    T whl[NH], whr[NH], shl, shr;
+    T wll[NL], wlr[NL], sll, slr;
+    T w3l[3][3], w3r[3][3], s3l[3], s3r[3];
+    T Phi[NH][(NH + 1) / 2], Psum_hi[NH];
+    T Plo[NL][(NL + 1) / 2], Psum_lo[NL];
+    T P3[3][2], Psum3[3];
+    T g_hi, g_hi1, ig_hi;   // gamma_HI, 1 - gamma_HI, 1 / gamma_HI
+    T g3[3];                // gamma_m = ((1-gHI)(1-gLO)/2, (1-gHI) gLO, (1-gHI)(1-gLO)/2)
+};
+
+// (eps + beta)^-p with the FP32 floor on eps + beta (as for GP-WENO)
+template <typename T>
+__device__ __forceinline__ T inv_pow(T eps, T beta, int p)
+{
+    const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(eps, beta), Num<T>::eps_floor()));
+    return p == 2 ? Num<T>::mul_rn(x, x) : x;
+}
+
+// sum_h (P_h . (f - shift))^2 over the N-point window f[w..w+N-1] of data
+// f_j = f_c + d_j (d_R = 0), P in half form (rows alternately symmetric and
+// skew), pf_h = (f_c - shift) sum_j P_hj supplied by the caller.
+template <typename T, int N, int R, int NS>
+__device__ __forceinline__ T beta_window(const T (&Ph)[N][(N + 1) / 2], const T (&d)[NS], int w, const T (&pf)[N])
+{
+    constexpr int HALF = N / 2;
+    T ps[HALF], ms[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+        const int lo = w + j, hi = w + N - 1 - j;
+        ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : d[lo] + d[hi]);
+        ms[j] = lo == R ? -d[hi] : (hi == R ? d[lo] : d[lo] - d[hi]);
+    }
+    T beta = T(0);
+#pragma unroll
+    for (int h = 0; h < N; ++h) {
+        T dot;
+        if (h % 2 == 0) {
+            dot = pf[h];
+            if (N % 2 == 1 && w + HALF != R) dot = fma(Ph[h][HALF], d[w + HALF], dot);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) dot = fma(Ph[h][j], ps[j], dot);
+        } else {
+            dot = Ph[h][0] * ms[0];
+#pragma unroll
+            for (int j = 1; j < HALF; ++j) dot = fma(Ph[h][j], ms[j], dot);
+        }
+        beta = fma(dot, dot, beta);
+    }
+    return beta;
+}
+
+// GP-AO(R,3) of Eq. GP-AO: the high-order prediction qh, with xh = (eps + beta^R)^-p,
+// hybridised with the three 3-point predictions q3 (x3 likewise); weights of Eq.
+// nonlin-AO with gamma_HI for the high-order stencil and gamma_m for the small ones.
+// The combination's coefficients sum to one, so predictions relative to cell s
+// combine to the hybrid relative to cell s.
+template <typename T, int R>
+__device__ __forceinline__ T ao_hybrid(const AoFaceTables<T, R> &ta, T qh, T xh, const T (&q3)[3], const T (&x3)[3])
+{
+    const T wh = ta.g_hi * xh;
+    T w[3], sum = wh;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        w[m] = ta.g3[m] * x3[m];
+        sum += w[m];
+    }
+    const T inv = Num<T>::rcp(sum);
+    const T r = wh * inv * ta.ig_hi;   // omega^R / gamma_HI
+    T q = r * qh;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) q = fma(fma(w[m], inv, -r * ta.g3[m]), q3[m], q);
+    return q;
+}
+
+// GP-AO prediction of one side of the face, relative to cell s, from the
+// characteristic data d (relative to cell s, d_R = 0) and the centre value fc:
+// left (RIGHT = false) from the stencil d[0..2R] of cell s at x* = +1/2, right
+// from d[1..2R+1] of cell s+1 at x* = -1/2.  beta of each stencil is the
+// data-fit term (1/2) f^T K_N(sigma)^-1 f of Eq. log-like, on f (zero mean) or
+// on f minus the side's centre value (MEAN).  R = 3 adds the recursive
+// hybridisation of AO(3,3) and AO(2,3) (Eqs. recursive-weights, AO-recursive).
+template <typename T, int R, int NS, bool RIGHT, bool MEAN>
+__device__ __forceinline__ T ao_side(const AoFaceTables<T, R> &ta, const T (&d)[NS], T fc)
+{
+    constexpr int NH = 2 * R + 1, NL = AoFaceTables<T, R>::NL;
+    constexpr int o = RIGHT ? 1 : 0;
+    const T shift = MEAN ? (RIGHT ? -d[R + 1] : T(0)) : fc;   // pf_h = Psum_h * shift
+    T q3[3], x3[3];
+    {
+        T pf[3];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) pf[h] = (h % 2 == 0) ? ta.Psum3[h] * shift : T(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const int w0 = o + R - 2 + m;   // Eq. cweno_stencil: cells c-2..c, c-1..c+1, c..c+2
+            T q = (RIGHT ? ta.s3r[m] : ta.s3l[m]) * fc;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (w0 + j != R) q = fma(RIGHT ? ta.w3r[m][j] : ta.w3l[m][j], d[w0 + j], q);
+            q3[m] = q;
+            x3[m] = inv_pow<T>(ta.eps, T(0.5) * beta_window<T, 3, R, NS>(ta.P3, d, w0, pf), ta.p);
+        }
+    }
+    T pfh[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) pfh[h] = (h % 2 == 0) ? ta.Psum_hi[h] * shift : T(0);
+    T qh = (RIGHT ? ta.shr : ta.shl) * fc;
+#pragma unroll
+    for (int j = 0; j < NH; ++j)
+        if (o + j != R) qh = fma(RIGHT ? ta.whr[j] : ta.whl[j], d[o + j], qh);
+    const T xh = inv_pow<T>(ta.eps, T(0.5) * beta_window<T, NH, R, NS>(ta.Phi, d, o, pfh), ta.p);
+    const T q_hi = ao_hybrid<T, R>(ta, qh, xh, q3, x3);
+    if constexpr (R == 2) {
+        return q_hi;
+    } else {
+        T pfl[NL];
+#pragma unroll
+        for (int h = 0; h < NL; ++h) pfl[h] = (h % 2 == 0) ? ta.Psum_lo[h] * shift : T(0);
+        T ql = (RIGHT ? ta.slr : ta.sll) * fc;
+#pragma unroll
+        for (int j = 0; j < NL; ++j)
+            if (o + 1 + j != R) ql = fma(RIGHT ? ta.wlr[j] : ta.wll[j], d[o + 1 + j], ql);
+        const T xl = inv_pow<T>(ta.eps, T(0.5) * beta_window<T, NL, R, NS>(ta.Plo, d, o + 1, pfl), ta.p);
+        const T q_lo = ao_hybrid<T, R>(ta, ql, xl, q3, x3);
+        const T vh = ta.g_hi * xh, vl = ta.g_hi1 * xl;
+        const T inv = Num<T>::rcp(vh + vl);
+        const T rh = vh * inv * ta.ig_hi;   // nu^R' / gamma_HI
+        return fma(rh, q_hi, fma(-rh, ta.g_hi1, vl * inv) * q_lo);
+    }
+}
+
 // One face, cell-relative form.  st[0..2R+1] is the normal-first conserved
 // stencil; the face s+1/2 lies between st[R] (cell s) and st[R+1] (cell s+1).
 // Outputs
@@ -298,7 +439,7 @@ __device__ __forceinline__ T beta_weight(const FaceTables<T, R> &tb, const T (&d
 //     V_{s+1} + R (q_R - L V_{s+1}), using R L = I and sum_m omega_m = 1;
 //   * fluxes and conserved states are perturbations about V_s (prim_pert).
 // Returns false on a non-physical Roe, left, right or neighbour state.
-template <typename T, int NC, int R, bool MEAN = false>
+template <typename T, int NC, int R, bool MEAN = false, bool AO = false>
 __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
                                          T (&B)[NC])
 {
@@ -330,6 +471,13 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
         T d[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) d[j] = (j == R) ? T(0) : f.lrow(kk, dV[j]);
+        if constexpr (AO) {
+            // GP-AO predictions relative to cell s (the kernel parameter is AoFaceTables)
+            const auto &ta = static_cast<const AoFaceTables<T, R> &>(tb);
+            dqL[kk] = ao_side<T, R, NS, false, MEAN>(ta, d, fc);                 // q_L - L V_s
+            dqR[kk] = ao_side<T, R, NS, true, MEAN>(ta, d, fc) - d[R + 1];      // q_R - L V_{s+1}
+            continue;
+        }
 
         // zero mean: both sides shift by f_c, so the right side's window m is the
         // left side's window m+1 and the R+2 windows are shared.  Mean f_centre:
@@ -589,15 +737,19 @@ __device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const Fac
 }
 
 // Scheme variants chosen at compile time: bit 0 the non-zero-mean smoothness
-// indicators, bit 1 the FD-Flux form.
-constexpr int kVarMean = 1, kVarFdFlux = 2;
+// indicators, bit 1 the FD-Flux form, bit 2 GP-AO.
+constexpr int kVarMean = 1, kVarFdFlux = 2, kVarAo = 4;
+
+// Kernel parameter type of a variant's tables.
+template <typename T, int R, int VAR>
+using TablesFor = typename std::conditional<(VAR & kVarAo) != 0, AoFaceTables<T, R>, FaceTables<T, R>>::type;
 
 template <typename T, int NC, int R, int VAR>
 __device__ __forceinline__ bool face_eval(const T (&st)[2 * R + 2][NC], const FaceTables<T, R> &tb, T (&A)[NC],
                                           T (&B)[NC])
 {
     if constexpr ((VAR & kVarFdFlux) != 0) return face_fdf<T, NC, R, (VAR & kVarMean) != 0>(st, tb, A, B);
-    else return face_rel<T, NC, R, (VAR & kVarMean) != 0>(st, tb, A, B);
+    else return face_rel<T, NC, R, (VAR & kVarMean) != 0, (VAR & kVarAo) != 0>(st, tb, A, B);
 }
 
 // Weights of the corrected-flux difference: with the face-flux correction

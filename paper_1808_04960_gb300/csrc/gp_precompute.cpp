@@ -327,7 +327,7 @@ bool gp_weights(dd q, const int *pts2, int n, int xs2, dd *w, double *cond, cons
 
 // Cyclic Jacobi eigen-decomposition of a small symmetric matrix in
 // double-double; textbook rotations (Golub & Van Loan, Alg. 8.4.2).
-void jacobi(dd A[kMaxS][kMaxS], int n, dd V[kMaxS][kMaxS])
+void jacobi(dd A[kMaxBig][kMaxBig], int n, dd V[kMaxBig][kMaxBig])
 {
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) V[i][j] = make(i == j ? 1.0 : 0.0);
@@ -431,6 +431,61 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
     return true;
 }
 
+// Smoothness factors of the N-point covariance K_N(sigma) (points 0..N-1):
+// P[h*N + j] = v_h[j] / sqrt(lambda_h) with lambda ascending, the half form
+// Ph[k*N + j] (j < (N+1)/2, largest lambda first, symmetric and skew rows
+// alternating -- checked), the row sums Psum (zero for skew rows) and
+// log det K_N.
+bool eigen_factors(dd qs, int N, double *P, double *lambda, double *Ph, double *Psum, double *logdet, char *err,
+                   std::size_t errlen)
+{
+    dd Ks[kMaxBig][kMaxBig], V[kMaxBig][kMaxBig];
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) Ks[a][b] = se_entry(qs, 2 * a, 2 * b);
+    jacobi(Ks, N, V);
+    int order[kMaxBig];
+    for (int h = 0; h < N; ++h) order[h] = h;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            if (Ks[order[b]][order[b]].hi < Ks[order[a]][order[a]].hi) {
+                int t = order[a];
+                order[a] = order[b];
+                order[b] = t;
+            }
+    double ld = 0.0;
+    for (int h = 0; h < N; ++h) {
+        int e = order[h];
+        dd lam = Ks[e][e];
+        if (!(lam.hi > 0.0)) {
+            std::snprintf(err, errlen, "K_%d(sigma) has a non-positive eigenvalue", N);
+            return false;
+        }
+        lambda[h] = to_d(lam);
+        ld += std::log(lambda[h]);
+        dd rs = div(make(1.0), sqrt_dd(lam));
+        for (int j = 0; j < N; ++j) P[h * N + j] = to_d(mul(V[j][e], rs));
+    }
+    if (logdet) *logdet = ld;
+    // half form, descending lambda, with the symmetric/skew alternation checked
+    for (int k = 0; k < N; ++k) {
+        const double *row = P + (N - 1 - k) * N;
+        double scale = 0.0;
+        for (int j = 0; j < N; ++j) scale = std::fmax(scale, std::fabs(row[j]));
+        const double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+        for (int j = 0; j < N; ++j)
+            if (std::fabs(row[j] - sgn * row[N - 1 - j]) > 1e-12 * scale) {
+                std::snprintf(err, errlen, "eigenvector %d of K_%d(sigma) is not %s", k, N,
+                              k % 2 == 0 ? "symmetric" : "skew-symmetric");
+                return false;
+            }
+        for (int j = 0; j < (N + 1) / 2; ++j) Ph[k * N + j] = row[j];
+        dd sum = make(0.0);
+        for (int j = 0; j < N; ++j) sum = add(sum, make(row[j]));
+        Psum[k] = (k % 2 == 0) ? to_d(sum) : 0.0;
+    }
+    return true;
+}
+
 }  // namespace
 
 int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std::size_t errlen, int poly, int recon)
@@ -470,47 +525,56 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
         return 2;
     }
     // smoothness-indicator covariance K_m(sigma) on the points 0..R
-    dd Ks[kMaxS][kMaxS], V[kMaxS][kMaxS];
-    for (int a = 0; a < S; ++a)
-        for (int b = 0; b < S; ++b) Ks[a][b] = se_entry(qs, 2 * a, 2 * b);
-    jacobi(Ks, S, V);
-    int order[kMaxS];
-    for (int h = 0; h < S; ++h) order[h] = h;
-    for (int a = 0; a < S; ++a)
-        for (int b = a + 1; b < S; ++b)
-            if (Ks[order[b]][order[b]].hi < Ks[order[a]][order[a]].hi) {
-                int t = order[a];
-                order[a] = order[b];
-                order[b] = t;
+    if (!eigen_factors(qs, S, out->P, out->lambda, out->Ph, out->Psum, nullptr, err, errlen)) return 2;
+    return 0;
+}
+
+int ao_precompute(int R, double ell, double sigma, AoTables *out, char *err, std::size_t errlen)
+{
+    if (R != 2 && R != 3) {
+        std::snprintf(err, errlen, "GP-AO needs R = 2 (AO(2,3)) or R = 3 (AO(3,2,3)), got %d", R);
+        return 1;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->R = R;
+    dd ql = exp_dd(neg(div(make(1.0), mul_d(mul(make(ell), make(ell)), 8.0))));
+    dd qs = exp_dd(neg(div(make(1.0), mul_d(mul(make(sigma), make(sigma)), 8.0))));
+    WeightKind kind;
+    kind.poly = 0;
+    kind.recon = 0;
+    kind.a = make(0.0);
+    // GP weights of one stencil (cells lo..hi relative to the centre) at x* = +-1/2, and sum - 1
+    auto weights = [&](int lo, int hi, double *wl, double *wr, double *sl, double *sr) {
+        int p2[kMaxBig];
+        const int n = hi - lo + 1;
+        for (int j = 0; j < n; ++j) p2[j] = 2 * (lo + j);
+        dd w[kMaxBig];
+        for (int side = 0; side < 2; ++side) {
+            if (!gp_weights(ql, p2, n, side == 0 ? 1 : -1, w, nullptr, kind)) return false;
+            dd acc = make(-1.0);
+            for (int j = 0; j < n; ++j) {
+                (side == 0 ? wl : wr)[j] = to_d(w[j]);
+                acc = add(acc, w[j]);
             }
-    for (int h = 0; h < S; ++h) {
-        int e = order[h];
-        dd lam = Ks[e][e];
-        if (!(lam.hi > 0.0)) {
-            std::snprintf(err, errlen, "K_m(sigma) has a non-positive eigenvalue");
-            return 2;
+            *(side == 0 ? sl : sr) = to_d(acc);
         }
-        out->lambda[h] = to_d(lam);
-        dd rs = div(make(1.0), sqrt_dd(lam));
-        for (int j = 0; j < S; ++j) out->P[h * S + j] = to_d(mul(V[j][e], rs));
+        return true;
+    };
+    bool ok = weights(-R, R, out->w_hi_l, out->w_hi_r, &out->s_hi_l, &out->s_hi_r);
+    if (R == 3) ok = ok && weights(-(R - 1), R - 1, out->w_lo_l, out->w_lo_r, &out->s_lo_l, &out->s_lo_r);
+    for (int m = 0; m < 3; ++m)   // Eq. cweno_stencil: cells i-2..i, i-1..i+1, i..i+2
+        ok = ok && weights(m - 2, m, out->w3_l + 3 * m, out->w3_r + 3 * m, out->s3_l + m, out->s3_r + m);
+    if (!ok) {
+        std::snprintf(err, errlen, "a GP-AO stencil covariance is not positive definite in double-double");
+        return 2;
     }
-    // half form, descending lambda, with the symmetric/skew alternation checked
-    for (int k = 0; k < S; ++k) {
-        const double *row = out->P + (S - 1 - k) * S;
-        double scale = 0.0;
-        for (int j = 0; j < S; ++j) scale = std::fmax(scale, std::fabs(row[j]));
-        const double sgn = (k % 2 == 0) ? 1.0 : -1.0;
-        for (int j = 0; j < S; ++j)
-            if (std::fabs(row[j] - sgn * row[S - 1 - j]) > 1e-12 * scale) {
-                std::snprintf(err, errlen, "eigenvector %d of K_m(sigma) is not %s", k,
-                              k % 2 == 0 ? "symmetric" : "skew-symmetric");
-                return 2;
-            }
-        for (int j = 0; j < (S + 1) / 2; ++j) out->Ph[k * S + j] = row[j];
-        dd sum = make(0.0);
-        for (int j = 0; j < S; ++j) sum = add(sum, make(row[j]));
-        out->Psum[k] = (k % 2 == 0) ? to_d(sum) : 0.0;
-    }
+    double lam[kMaxBig];
+    if (!eigen_factors(qs, 2 * R + 1, out->P_hi, lam, out->Ph_hi, out->Psum_hi, &out->logdet_hi, err, errlen))
+        return 2;
+    if (R == 3 && !eigen_factors(qs, 2 * R - 1, out->P_lo, lam, out->Ph_lo, out->Psum_lo, &out->logdet_lo, err,
+                                 errlen))
+        return 2;
+    if (!eigen_factors(qs, 3, out->P_3, lam, out->Ph_3, out->Psum_3, &out->logdet_3, err, errlen)) return 2;
     return 0;
 }
 

@@ -44,4 +44,22 @@ struct GpTables {
 int gp_precompute(int R, double ell_over_dx, double sigma_over_dx, GpTables *out, char *err, std::size_t errlen,
                   int poly = 0, int recon = 0);
 
+// GP-AO tables (Appendix A): R = 2 serves AO(2,3), R = 3 the recursive
+// AO(3,2,3).  GP weights of the full stencil S_R (hi), of S_{R-1} (lo, R = 3
+// only) and of the three 3-point stencils of Eq. cweno_stencil (w3[m][j]),
+// for the left (x* = +1/2) and right (x* = -1/2) states, each with its sum
+// minus one; the smoothness factors of K_N(sigma) for N = 2R+1, 2R-1 and 3
+// (full and half form as in GpTables, rows of length N) and log det K_N.
+struct AoTables {
+    int R;
+    double w_hi_l[kMaxBig], w_hi_r[kMaxBig], s_hi_l, s_hi_r;
+    double w_lo_l[kMaxBig], w_lo_r[kMaxBig], s_lo_l, s_lo_r;
+    double w3_l[9], w3_r[9], s3_l[3], s3_r[3];
+    double P_hi[kMaxBig * kMaxBig], Ph_hi[kMaxBig * kMaxBig], Psum_hi[kMaxBig], logdet_hi;
+    double P_lo[kMaxBig * kMaxBig], Ph_lo[kMaxBig * kMaxBig], Psum_lo[kMaxBig], logdet_lo;
+    double P_3[9], Ph_3[9], Psum_3[3], logdet_3;
+};
+
+int ao_precompute(int R, double ell_over_dx, double sigma_over_dx, AoTables *out, char *err, std::size_t errlen);
+
 }  // namespace gpweno

@@ -23,6 +23,7 @@ struct gpweno_plan_s {
     double gamma = 1.4;
     gpweno_opts opts{};
     gpweno::GpTables tab{};
+    gpweno::AoTables ao{};                  // GP-AO tables when opts.ao = 1
     int device = 0;
     int num_sms = 0;
     long ncell = 0;
@@ -78,13 +79,18 @@ gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, 
 // dispatch entry points implemented in stage_f32.cu / stage_f64.cu
 gpweno_status launch_stage_f32(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64(gpweno_plan p, const StageIO &io, cudaStream_t st);
-// variants: 1 non-zero-mean beta, 2 FD-Flux, 3 both (kVarMean | kVarFdFlux)
+// variants (kVarMean = 1 non-zero-mean beta, kVarFdFlux = 2 FD-Flux, kVarAo = 4 GP-AO):
+// 1, 2, 3 = FD-Flux with mean, 4 = AO, 5 = AO with mean
 gpweno_status launch_stage_f32_var1(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f32_var2(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f32_var3(gpweno_plan p, const StageIO &io, cudaStream_t st);
+gpweno_status launch_stage_f32_var4(gpweno_plan p, const StageIO &io, cudaStream_t st);
+gpweno_status launch_stage_f32_var5(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64_var1(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64_var2(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64_var3(gpweno_plan p, const StageIO &io, cudaStream_t st);
+gpweno_status launch_stage_f64_var4(gpweno_plan p, const StageIO &io, cudaStream_t st);
+gpweno_status launch_stage_f64_var5(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_max_rate_f32(gpweno_plan p, const void *U, cudaStream_t st);
 gpweno_status launch_max_rate_f64(gpweno_plan p, const void *U, cudaStream_t st);
 gpweno_status launch_batch_stage_f32(gpweno_plan batch, int stage, void *const *U, void *const *scratch,

@@ -317,7 +317,7 @@ __device__ __forceinline__ void finish_block(const StageArgs<T> &a, T r0, T r1, 
 }
 
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
 // overwrites cell by cell (each cell reads its own P first), so 3D needs no
 // scratch beyond 2D's.
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
@@ -502,7 +502,7 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
 }
 
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
@@ -536,7 +536,7 @@ constexpr size_t stage1d_smem_bytes()
 }
 
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, FaceTables<T, R> tb)
+__global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     constexpr int G = R + 3, NC = 3, NS = 2 * R + 2;
     constexpr int STRIDE = NT - 5 + 2 * G;

@@ -8,11 +8,13 @@ namespace gpweno {
 
 gpweno_status launch_stage_f64(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    const int var = (p->opts.beta_mean ? kVarMean : 0) | (p->opts.scheme ? kVarFdFlux : 0);
+    const int var = (p->opts.beta_mean ? kVarMean : 0) | (p->opts.scheme ? kVarFdFlux : 0) | (p->opts.ao ? kVarAo : 0);
     switch (var) {
     case kVarMean: return launch_stage_f64_var1(p, io, st);
     case kVarFdFlux: return launch_stage_f64_var2(p, io, st);
     case kVarFdFlux | kVarMean: return launch_stage_f64_var3(p, io, st);
+    case kVarAo: return launch_stage_f64_var4(p, io, st);
+    case kVarAo | kVarMean: return launch_stage_f64_var5(p, io, st);
     default: return launch_stage_T<double, 0>(p, io, st);
     }
 }

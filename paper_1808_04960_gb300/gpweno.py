@@ -36,7 +36,8 @@ class Dims(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("sigma_over_dx", ctypes.c_double), ("eps", ctypes.c_double), ("p", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("cfl", ctypes.c_double), ("flux_form", ctypes.c_int),
-                ("beta_mean", ctypes.c_int), ("candidates", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("beta_mean", ctypes.c_int), ("candidates", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("ao", ctypes.c_int), ("ao_gamma_hi", ctypes.c_double), ("ao_gamma_lo", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -62,6 +63,7 @@ def load(path: str | None = None):
             "gpweno_plan_destroy": (i, [vp]),
             "gpweno_plan_tables": (i, [vp, dp, dp, dp, dp]),
             "gpweno_gp_tables": (i, [i, d, d, i, i, dp, dp, dp, dp, dp, dp]),
+            "gpweno_ao_tables": (i, [i, d, d, dp, dp, dp, dp, dp, dp]),
             "gpweno_rhs": (i, [vp, vp, vp, vp]),
             "gpweno_rk3_step": (i, [vp, vp, vp, d, vp, vp]),
             "gpweno_cfl_dt": (i, [vp, vp, d, vp, vp]),
@@ -116,6 +118,21 @@ def gp_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0, candidates
                 w_sub_r=a(wmr, (S, S)), gamma_r=a(gr, (S,)))
 
 
+def ao_tables(R: int, ell_over_dx: float, sigma_over_dx: float = 3.0) -> dict:
+    """The library's double-double GP-AO tables, computed on the host (no device needed)."""
+    import numpy as np
+    nh, nl = 2 * R + 1, 2 * R - 1
+    wh, wl, w3 = _dbl(2 * nh), _dbl(2 * nl), _dbl(18)
+    Ph, Pl, P3 = _dbl(nh * nh), _dbl(nl * nl), _dbl(9)
+    _check(load().gpweno_ao_tables(int(R), float(ell_over_dx), float(sigma_over_dx), wh, wl, w3, Ph, Pl, P3),
+           "gpweno_ao_tables")
+    a = lambda x, shape: np.array(list(x), dtype=np.float64).reshape(shape)
+    out = dict(w_hi=a(wh, (2, nh)), w_3=a(w3, (2, 3, 3)), P_hi=a(Ph, (nh, nh)), P_3=a(P3, (3, 3)))
+    if R == 3:
+        out.update(w_lo=a(wl, (2, nl)), P_lo=a(Pl, (nl, nl)))
+    return out
+
+
 def _stream_handle(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -136,7 +153,8 @@ class Plan:
     """
 
     def __init__(self, R, ell_over_dx, shape, dx, bc, gamma=1.4, sigma_over_dx=3.0, eps=1e-36, p=2,
-                 dtype="f32", cfl=0.0, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim"):
+                 dtype="f32", cfl=0.0, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim", ao=False,
+                 ao_gamma_hi=0.85, ao_gamma_lo=0.85):
         import torch
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
@@ -165,6 +183,9 @@ class Plan:
         opts.beta_mean = 1 if beta_mean else 0
         opts.candidates = {"gp": 0, "poly": 1}[candidates]
         opts.scheme = {"fdprim": 0, "fdflux": 1}[scheme]
+        opts.ao = 1 if ao else 0
+        opts.ao_gamma_hi = float(ao_gamma_hi)
+        opts.ao_gamma_lo = float(ao_gamma_lo)
         h = ctypes.c_void_p()
         _check(self.lib.gpweno_plan_create(ctypes.byref(h), self.R, float(ell_over_dx), ctypes.byref(dims),
                                            float(gamma), ctypes.byref(opts)), "gpweno_plan_create")

@@ -102,8 +102,8 @@ def test_dd_poly_tables_match_oracle(lib, R):
 
 
 def test_variant_options_checked(lib):
-    """beta_mean, candidates and scheme outside {0, 1}, and FD-Flux with a face solver, are refused
-    by the C ABI before any device work."""
+    """beta_mean, candidates, scheme and ao outside {0, 1}, FD-Flux with a face solver, GP-AO with
+    FD-Flux, and gamma_HI outside (0, 1) are refused by the C ABI before any device work."""
     import ctypes
     with pytest.raises(gpweno.GpwenoError) as e:
         gpweno._check(lib.gpweno_gp_tables(2, 12.0, 3.0, 2, 0, None, None, None, None, None, None), "gp_tables")
@@ -117,11 +117,16 @@ def test_variant_options_checked(lib):
         dims.n[a] = 16 if a < 2 else 1
         dims.dx[a] = 0.1
         dims.bc_lo[a] = dims.bc_hi[a] = 0
-    for field, val in (("beta_mean", 3), ("candidates", 3), ("scheme", 2), ("flux_form", 3), ("scheme+flux", 1)):
+    for field, val in (("beta_mean", 3), ("candidates", 3), ("scheme", 2), ("flux_form", 3), ("scheme+flux", 1),
+                       ("ao", 2), ("ao+scheme", 1), ("ao_gamma", 1.0)):
         o = gpweno.Opts()
         lib.gpweno_default_opts(ctypes.byref(o))
         if field == "scheme+flux":
             o.scheme, o.flux_form = 1, 1
+        elif field == "ao+scheme":
+            o.ao, o.scheme = 1, 1
+        elif field == "ao_gamma":
+            o.ao, o.ao_gamma_hi = 1, 1.0
         else:
             setattr(o, field, val)
         h = ctypes.c_void_p()
@@ -146,3 +151,23 @@ def test_dd_recon_tables_match_oracle(lib, R, ell):
     op = OT.tables(R, ell, 3.0, 0.5, poly=True, recon=True)
     np.testing.assert_allclose(tp["w_sub"], op["w_sub"], rtol=0, atol=1e-15 * np.abs(op["w_sub"]).max())
     np.testing.assert_allclose(tp["gamma"], op["gamma"], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("R,ell", [(2, 12.0), (3, 12.0), (3, 6.0)])
+def test_dd_ao_tables_match_oracle(lib, R, ell):
+    """GP-AO tables: the library's double-double weights of the three stencil sizes and the
+    K_N(sigma) factors (P^T P = K_N^-1) against the oracle's 100-digit ones."""
+    t = gpweno.ao_tables(R, ell, 3.0)
+    for side, xs in ((0, 0.5), (1, -0.5)):
+        o = OT.ao_tables(R, ell, 3.0, xs)
+        np.testing.assert_allclose(t["w_hi"][side], o["w_hi"], rtol=0, atol=1e-13 * np.abs(o["w_hi"]).max())
+        np.testing.assert_allclose(t["w_3"][side], o["w_3"], rtol=0, atol=1e-13 * np.abs(o["w_3"]).max())
+        if R == 3:
+            np.testing.assert_allclose(t["w_lo"][side], o["w_lo"], rtol=0, atol=1e-13 * np.abs(o["w_lo"]).max())
+    o = OT.ao_tables(R, ell, 3.0, 0.5)
+    keys = ("hi", "lo", "3") if R == 3 else ("hi", "3")
+    for k in keys:
+        P = t["P_" + k]
+        np.testing.assert_allclose(P.T @ P, o["Kinv_" + k], rtol=0, atol=1e-11 * np.abs(o["Kinv_" + k]).max())
+    with pytest.raises(gpweno.GpwenoError):
+        gpweno.ao_tables(1, 12.0, 3.0)
