@@ -37,6 +37,25 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
     return t;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the stream's preceding kernel finishes; the stage kernels wait for it
+// (pdl_enter) before any global access.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Tables of a scheme variant: GP-AO adds its own on top of the GP-WENO ones.
 template <typename T, int R, int VAR>
 TablesFor<T, R, VAR> make_tables_var(const gpweno_plan_s *p)
@@ -157,8 +176,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
             pa.rate = nullptr;
             const long long rows = (long long)pa.nstrips * a.n[1] * a.n[2];
             const int grid = (int)std::max(1LL, std::min<long long>((long long)occ * p->num_sms, rows / 8));
-            kern<<<grid, NT, smem, st>>>(pa, tb);
-            cudaError_t e = cudaGetLastError();
+            cudaError_t e = launch_pdl(kern, grid, NT, smem, st, pa, tb);
             if (e != cudaSuccess) return cuda_fail(e, "plane3d kernel launch");
             count_launch(1);
         }
@@ -176,7 +194,8 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
             }
             const long long cols = ((long long)a.n[0] * a.n[1] + NT - 1) / NT * a.n[2];
             const int grid = (int)std::max(1LL, std::min<long long>((long long)occ * p->num_sms, cols / 8));
-            kern<<<grid, NT, smem, st>>>(a, tb);
+            cudaError_t e = launch_pdl(kern, grid, NT, smem, st, a, tb);
+            if (e != cudaSuccess) return cuda_fail(e, "stagez kernel launch");
         }
     } else if (p->dims.ndim == 2) {
         constexpr int NT = kNT2D;
@@ -196,7 +215,8 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         a.H = s.H;
         a.nseg = s.nseg;
         p->sched = s;
-        kern<<<s.grid, NT, smem, st>>>(a, tb);
+        cudaError_t e = launch_pdl(kern, s.grid, NT, smem, st, a, tb);
+        if (e != cudaSuccess) return cuda_fail(e, "stage2d kernel launch");
     } else {
         constexpr int NT = kNT1D;
         const size_t smem = stage1d_smem_bytes<T, R, NT>();
@@ -205,7 +225,8 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         a.W = (a.n[0] + a.nstrips - 1) / a.nstrips;
         a.H = 1;
         a.nseg = 1;
-        kern<<<a.nstrips, NT, smem, st>>>(a, tb);
+        cudaError_t e = launch_pdl(kern, a.nstrips, NT, smem, st, a, tb);
+        if (e != cudaSuccess) return cuda_fail(e, "stage1d kernel launch");
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");

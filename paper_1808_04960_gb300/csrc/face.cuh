@@ -476,42 +476,41 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             const auto &ta = static_cast<const AoFaceTables<T, R> &>(tb);
             dqL[kk] = ao_side<T, R, NS, false, MEAN>(ta, d, fc);                 // q_L - L V_s
             dqR[kk] = ao_side<T, R, NS, true, MEAN>(ta, d, fc) - d[R + 1];      // q_R - L V_{s+1}
-            continue;
-        }
-
-        // zero mean: both sides shift by f_c, so the right side's window m is the
-        // left side's window m+1 and the R+2 windows are shared.  Mean f_centre:
-        // the left side's centre is cell s (no shift), the right side's is cell
-        // s+1 (shift by d_{R+1}), and the 2R+2 windows are separate.
-        T pfl[S], pfr[S];
+        } else {
+            // zero mean: both sides shift by f_c, so the right side's window m is the
+            // left side's window m+1 and the R+2 windows are shared.  Mean f_centre:
+            // the left side's centre is cell s (no shift), the right side's is cell
+            // s+1 (shift by d_{R+1}), and the 2R+2 windows are separate.
+            T pfl[S], pfr[S];
 #pragma unroll
-        for (int h = 0; h < S; ++h) {
-            pfl[h] = (h % 2 == 0 && !MEAN) ? tb.Psum[h] * fc : T(0);
-            pfr[h] = (h % 2 == 0) ? (MEAN ? -tb.Psum[h] * d[R + 1] : pfl[h]) : T(0);
-        }
-        // --- candidates relative to the centre cells and nonlinear weights ---
-        // omega_m ~ gamma_m (eps + beta_m)^-p  (Eq. weights); sum_m omega_m = 1 is used exactly.
-        T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
-        T xl = beta_weight<T, R, NS>(tb, d, 0, pfl);
-#pragma unroll
-        for (int m = 0; m <= R; ++m) {
-            const T xr = beta_weight<T, R, NS>(tb, d, m + 1, pfr);
-            T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
-#pragma unroll
-            for (int j = 0; j <= R; ++j) {
-                if (m + j != R) sl = fma(tb.wl[m][j], d[m + j], sl);
-                if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
+            for (int h = 0; h < S; ++h) {
+                pfl[h] = (h % 2 == 0 && !MEAN) ? tb.Psum[h] * fc : T(0);
+                pfr[h] = (h % 2 == 0) ? (MEAN ? -tb.Psum[h] * d[R + 1] : pfl[h]) : T(0);
             }
-            const T yl = Num<T>::mul_rn(tb.gl[m], xl);
-            const T yr = Num<T>::mul_rn(tb.gr[m], xr);
-            numL = fma(yl, sl, numL);
-            denL = Num<T>::add_rn(denL, yl);
-            numR = fma(yr, sr, numR);
-            denR = Num<T>::add_rn(denR, yr);
-            if (m < R) xl = MEAN ? beta_weight<T, R, NS>(tb, d, m + 1, pfl) : xr;
+            // --- candidates relative to the centre cells and nonlinear weights ---
+            // omega_m ~ gamma_m (eps + beta_m)^-p  (Eq. weights); sum_m omega_m = 1 is used exactly.
+            T numL = T(0), denL = T(0), numR = T(0), denR = T(0);
+            T xl = beta_weight<T, R, NS>(tb, d, 0, pfl);
+#pragma unroll
+            for (int m = 0; m <= R; ++m) {
+                const T xr = beta_weight<T, R, NS>(tb, d, m + 1, pfr);
+                T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
+#pragma unroll
+                for (int j = 0; j <= R; ++j) {
+                    if (m + j != R) sl = fma(tb.wl[m][j], d[m + j], sl);
+                    if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
+                }
+                const T yl = Num<T>::mul_rn(tb.gl[m], xl);
+                const T yr = Num<T>::mul_rn(tb.gr[m], xr);
+                numL = fma(yl, sl, numL);
+                denL = Num<T>::add_rn(denL, yl);
+                numR = fma(yr, sr, numR);
+                denR = Num<T>::add_rn(denR, yr);
+                if (m < R) xl = MEAN ? beta_weight<T, R, NS>(tb, d, m + 1, pfl) : xr;
+            }
+            dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
+            dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}
         }
-        dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
-        dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}
     }
 
     // --- back-projection: primitive states relative to cell s -------------

@@ -316,21 +316,52 @@ __device__ __forceinline__ void finish_block(const StageArgs<T> &a, T r0, T r1, 
     if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.flags, 1);
 }
 
+// Programmatic dependent launch: wait until the stream's preceding grid has
+// finished and its writes are visible (a no-op without a programmatic
+// dependency), then allow the stream's next kernel to be scheduled, so that its
+// launch overlaps this grid's tail.  Every global access comes after this.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// First row of CTA b in the cost-balanced split of the strip-major row order
+// [0, total) over `grid` CTAs.  A row costs 2 (one x- and one y-face per
+// column) and every strip start inside a range costs 5 more (the warm-up
+// y-face rows of a new segment), so rows [0, u) cost 2u + 5 floor((u-1)/ny);
+// CTA b starts at the first row where that reaches b/grid of the total.
+// Non-decreasing in b, 0 at b = 0 and total at b = grid, so the ranges
+// [start(b), start(b+1)) partition the rows.
+__device__ __forceinline__ long long balanced_start(int b, int grid, long long total, int ny, int nstrips)
+{
+    if (b <= 0) return 0;
+    if (b >= grid) return total;
+    const long long ctot = 2 * total + 5 * ((total - 1) / ny);
+    const long long c = (ctot * b + grid / 2) / grid;
+    for (int k = 0; k < nstrips; ++k) {
+        const long long lo = (long long)k * ny, hi = lo + ny;
+        if (2 * hi + 5LL * k >= c) return min(max((c - 5LL * k + 1) / 2, lo), hi);
+    }
+    return total;
+}
+
 template <typename T, int R, int NT, int VAR = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
+    pdl_enter();
     const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
     T rmx = T(0), rmy = T(0);
     bool ok = true;
-    // Balanced persistent schedule: the strips' rows, laid end to end
-    // (strip-major), are split into gridDim.x equal ranges; a range that
+    // Persistent schedule: the strips' rows, laid end to end (strip-major),
+    // are split into gridDim.x ranges of equal estimated cost; a range that
     // crosses a strip boundary becomes two segments.
     const int ny = a.n[1];
     const long long total = (long long)a.nstrips * ny;
-    long long u = total * blockIdx.x / gridDim.x;
-    const long long uend = total * (blockIdx.x + 1) / gridDim.x;
+    long long u = balanced_start(blockIdx.x, gridDim.x, total, ny, a.nstrips);
+    const long long uend = balanced_start(blockIdx.x + 1, gridDim.x, total, ny, a.nstrips);
     while (u < uend) {
         const int strip = (int)(u / ny);
         const int y0 = (int)(u - (long long)strip * ny);
@@ -354,6 +385,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(Sta
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
+    pdl_enter();
     T rmx = T(0), rmy = T(0);
     bool ok = true;
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
@@ -506,6 +538,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stagez_kernel(Stag
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
+    pdl_enter();
     const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
     T rm[3] = {T(0), T(0), T(0)};
     bool ok = true;
@@ -544,6 +577,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
     T *row = reinterpret_cast<T *>(smem_raw);  // [NC][STRIDE]
     T *FA = row + NC * STRIDE;                 // [NC][NT]
     T *FB = FA + NC * NT;                      // [NC][NT]
+    pdl_enter();
     const T dt = a.dt_dev ? (T)(*a.dt_dev) : (T)a.dt;
     const int tid = threadIdx.x;
     const int nx = a.n[0];
