@@ -419,6 +419,49 @@ __device__ __forceinline__ T ao_side(const AoFaceTables<T, R> &ta, const T (&d)[
     }
 }
 
+// Packed FP32: two characteristic fields per instruction (fma/add/mul .f32x2
+// of sm_100 and later).  Each lane rounds exactly as the scalar operation.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// beta_weight for two fields at once: (eps + beta)^-p of window d[w..w+R] in each lane.
+template <int R, int NS>
+__device__ __forceinline__ float2 beta_weight2(const FaceTables<float, R> &tb, const float2 (&d)[NS], int w,
+                                               const float2 (&pf)[R + 1])
+{
+    constexpr int S = R + 1, HALF = S / 2;
+    float2 ps[HALF > 0 ? HALF : 1], ms[HALF > 0 ? HALF : 1];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+        const int lo = w + j, hi = w + S - 1 - j;
+        ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : add2(d[lo], d[hi]));
+        ms[j] = lo == R ? mul2(d[hi], f2(-1.0f)) : (hi == R ? d[lo] : sub2(d[lo], d[hi]));
+    }
+    float2 beta = f2(0.0f);
+#pragma unroll
+    for (int h = 0; h < S; ++h) {
+        float2 dot;
+        if (h % 2 == 0) {
+            dot = pf[h];
+            if (S % 2 == 1 && w + HALF != R) dot = fma2(f2(tb.Ph[h][HALF]), d[w + HALF], dot);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) dot = fma2(f2(tb.Ph[h][j]), ps[j], dot);
+        } else {
+            dot = mul2(f2(tb.Ph[h][0]), ms[0]);
+#pragma unroll
+            for (int j = 1; j < HALF; ++j) dot = fma2(f2(tb.Ph[h][j]), ms[j], dot);
+        }
+        beta = fma2(dot, dot, beta);
+    }
+    const float2 e = add2(f2(tb.eps), beta);
+    const float2 x = make_float2(Num<float>::rcp(fmaxf(e.x, Num<float>::eps_floor())),
+                                 Num<float>::rcp(fmaxf(e.y, Num<float>::eps_floor())));
+    return tb.p == 2 ? mul2(x, x) : x;
+}
+
 // One face, cell-relative form.  st[0..2R+1] is the normal-first conserved
 // stencil; the face s+1/2 lies between st[R] (cell s) and st[R+1] (cell s+1).
 // Outputs
@@ -465,6 +508,53 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
     }
 
     T dqL[NC], dqR[NC];
+    if constexpr (std::is_same<T, float>::value && !AO && NC == 4) {
+        // FP32 GP-WENO in 2D: the four fields in pairs (0,1), (2,3) through packed
+        // instructions (in 1D and 3D the odd field count would leave lanes idle and, in 3D,
+        // spill registers, so those keep the scalar loop).
+#pragma unroll
+        for (int k0 = 0; k0 < NC; k0 += 2) {
+            const int k1 = k0 + 1 < NC ? k0 + 1 : k0;
+            const float2 fc = make_float2(f.lrow(k0, f.Vs), f.lrow(k1, f.Vs));
+            float2 d[NS];
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                d[j] = (j == R) ? f2(0.0f) : make_float2(f.lrow(k0, dV[j]), f.lrow(k1, dV[j]));
+            float2 pfl[S], pfr[S];
+#pragma unroll
+            for (int h = 0; h < S; ++h) {
+                pfl[h] = (h % 2 == 0 && !MEAN) ? mul2(f2(tb.Psum[h]), fc) : f2(0.0f);
+                pfr[h] = (h % 2 == 0) ? (MEAN ? mul2(f2(-tb.Psum[h]), d[R + 1]) : pfl[h]) : f2(0.0f);
+            }
+            float2 numL = f2(0.0f), denL = f2(0.0f), numR = f2(0.0f), denR = f2(0.0f);
+            float2 xl = beta_weight2<R, NS>(tb, d, 0, pfl);
+#pragma unroll
+            for (int m = 0; m <= R; ++m) {
+                const float2 xr = beta_weight2<R, NS>(tb, d, m + 1, pfr);
+                float2 sl = mul2(f2(tb.sl1[m]), fc), sr = mul2(f2(tb.sr1[m]), fc);
+#pragma unroll
+                for (int j = 0; j <= R; ++j) {
+                    if (m + j != R) sl = fma2(f2(tb.wl[m][j]), d[m + j], sl);
+                    if (1 + m + j != R) sr = fma2(f2(tb.wr[m][j]), d[1 + m + j], sr);
+                }
+                const float2 yl = mul2(f2(tb.gl[m]), xl);
+                const float2 yr = mul2(f2(tb.gr[m]), xr);
+                numL = fma2(yl, sl, numL);
+                denL = add2(denL, yl);
+                numR = fma2(yr, sr, numR);
+                denR = add2(denR, yr);
+                if (m < R) xl = MEAN ? beta_weight2<R, NS>(tb, d, m + 1, pfl) : xr;
+            }
+            const float2 qL = mul2(numL, make_float2(Num<float>::rcp(denL.x), Num<float>::rcp(denL.y)));
+            const float2 qR = sub2(mul2(numR, make_float2(Num<float>::rcp(denR.x), Num<float>::rcp(denR.y))), d[R + 1]);
+            dqL[k0] = qL.x;
+            dqR[k0] = qR.x;
+            if (k1 != k0) {
+                dqL[k1] = qL.y;
+                dqR[k1] = qR.y;
+            }
+        }
+    } else {
 #pragma unroll
     for (int kk = 0; kk < NC; ++kk) {
         const T fc = f.lrow(kk, f.Vs);
@@ -511,6 +601,7 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
             dqR[kk] = numR * Num<T>::rcp(denR) - d[R + 1];   // q_R - L V_{s+1}
         }
+    }
     }
 
     // --- back-projection: primitive states relative to cell s -------------
