@@ -508,13 +508,16 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
     }
 
     T dqL[NC], dqR[NC];
-    if constexpr (std::is_same<T, float>::value && !AO && NC == 4) {
-        // FP32 GP-WENO in 2D: the four fields in pairs (0,1), (2,3) through packed
-        // instructions (in 1D and 3D the odd field count would leave lanes idle and, in 3D,
-        // spill registers, so those keep the scalar loop).
+    // FP32 GP-WENO in 1D and 2D: fields in pairs (0,1), (2,3) through packed
+    // instructions, an odd last field (1D) through the scalar loop below.  3D keeps
+    // the scalar loop: with five fields the packed form spills registers in the
+    // z-marching kernel and measured 3% slower.
+    constexpr bool kPacked = std::is_same<T, float>::value && !AO && NC <= 4;
+    constexpr int kScalarFrom = kPacked ? (NC / 2) * 2 : 0;
+    if constexpr (kPacked) {
 #pragma unroll
-        for (int k0 = 0; k0 < NC; k0 += 2) {
-            const int k1 = k0 + 1 < NC ? k0 + 1 : k0;
+        for (int k0 = 0; k0 + 1 < NC; k0 += 2) {
+            const int k1 = k0 + 1;
             const float2 fc = make_float2(f.lrow(k0, f.Vs), f.lrow(k1, f.Vs));
             float2 d[NS];
 #pragma unroll
@@ -549,14 +552,13 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
             const float2 qR = sub2(mul2(numR, make_float2(Num<float>::rcp(denR.x), Num<float>::rcp(denR.y))), d[R + 1]);
             dqL[k0] = qL.x;
             dqR[k0] = qR.x;
-            if (k1 != k0) {
-                dqL[k1] = qL.y;
-                dqR[k1] = qR.y;
-            }
+            dqL[k1] = qL.y;
+            dqR[k1] = qR.y;
         }
-    } else {
+    }
+    {
 #pragma unroll
-    for (int kk = 0; kk < NC; ++kk) {
+    for (int kk = kScalarFrom; kk < NC; ++kk) {
         const T fc = f.lrow(kk, f.Vs);
         T d[NS];
 #pragma unroll
