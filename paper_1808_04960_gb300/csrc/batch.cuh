@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT)
         const T dt = sdt;
         const int tab = stab;
         switch (sR) {
-        case 1: stage2d_segment<T, 1, NT>(sa, bt.t1[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
-        case 2: stage2d_segment<T, 2, NT>(sa, bt.t2[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
-        default: stage2d_segment<T, 3, NT>(sa, bt.t3[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        case 1: stage2d_segment<T, 1, NT, 4, 0, true>(sa, bt.t1[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        case 2: stage2d_segment<T, 2, NT, 4, 0, true>(sa, bt.t2[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        default: stage2d_segment<T, 3, NT, 4, 0, true>(sa, bt.t3[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
         }
         // the segment ends with a barrier, so thread 0 may overwrite the shared arguments
     }

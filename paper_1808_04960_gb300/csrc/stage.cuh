@@ -148,7 +148,11 @@ __device__ __forceinline__ void rates2d(const T (&u)[4], T gam, const T (&idx)[3
 
 // One segment: rows [y0, y1) of strip `strip` of the xy-plane starting at cell offset zoff.
 // NC = 4 (2D) or 5 (an xy-plane of a 3D grid).
-template <typename T, int R, int NT, int NC = 4, int VAR = 0>
+// ONE_SITE: evaluate the y- and x-face through one copy of the face routine (a
+// loop of two passes) instead of two inlined copies.  Two copies let the compiler
+// interleave the two independent faces (faster for the 2D kernel); one copy halves
+// the code, which pays where several radii share a kernel (batch) and in 3D.
+template <typename T, int R, int NT, int NC = 4, int VAR = 0, bool ONE_SITE = false>
 __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, int strip, int y0,
                                                 int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok, long zoff = 0)
 {
@@ -213,50 +217,101 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             lov[c] = (epi && a.lo && a.mode == kModeFinal) ? a.lo[c * plane + cell] : T(0);
         }
 
-        // ---- y-face s+1/2 of column tid --------------------------------
-        if (col_ok) {
-            T st[NS][NC];
+        if constexpr (ONE_SITE) {
+            // ---- y-face s+1/2 of column tid (pass 0) and x-face tid of output row r (pass 1),
+            // through one copy of the face routine ------------------------------
+            const bool do_y = col_ok, do_x = out_row && tid < Wc + 5;
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 0 ? !do_y : !do_x) continue;
+                // stencil element (q, c): ring + off[q] + comp[c] * STRIDE, normal-first
+                int off[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const T *row = ring + RG::slot(s - R + q) * (NC * STRIDE) + G + tid;
-                // normal-first for a y-face: (rho, rho v, rho u, [rho w], E)
+                for (int q = 0; q < NS; ++q)
+                    off[q] = pass == 0 ? RG::slot(s - R + q) * (NC * STRIDE) + G + tid : RG::slot(r) * (NC * STRIDE) + tid + q;
+                T st[NS][NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) st[q][c] = row[(c == 1 ? 2 : (c == 2 ? 1 : c)) * STRIDE];
+                for (int q = 0; q < NS; ++q)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        // a y-face's normal is the second velocity: (rho, rho v, rho u, [rho w], E)
+                        const int cc = pass == 0 ? (c == 1 ? 2 : (c == 2 ? 1 : c)) : c;
+                        st[q][c] = ring[off[q] + cc * STRIDE];
+                    }
+                T An[NC], Bn[NC];
+                ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
+                if (pass == 0) {
+                    T Ac[NC], Bc[NC];   // back to natural order
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const int pc = c == 1 ? 2 : (c == 2 ? 1 : c);
+                        Ac[c] = An[pc];
+                        Bc[c] = Bn[pc];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) Dy[k][c] = Dy[k + 1][c];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        Dy[4][c] = Ac[c] - Ap[c] + Bp[c];   // jump across row s (valid once s > s_begin)
+                        Ap[c] = Ac[c];
+                        Bp[c] = Bc[c];
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        FA[c * NT + tid] = An[c];
+                        FB[c * NT + tid] = Bn[c];
+                    }
+                }
             }
-            T An[NC], Bn[NC];
-            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
-            T Ac[NC], Bc[NC];   // back to natural order
+        } else {
+            // ---- y-face s+1/2 of column tid --------------------------------
+            if (col_ok) {
+                T st[NS][NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int pc = c == 1 ? 2 : (c == 2 ? 1 : c);
-                Ac[c] = An[pc];
-                Bc[c] = Bn[pc];
+                for (int q = 0; q < NS; ++q) {
+                    const T *row = ring + RG::slot(s - R + q) * (NC * STRIDE) + G + tid;
+                    // normal-first for a y-face: (rho, rho v, rho u, [rho w], E)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) st[q][c] = row[(c == 1 ? 2 : (c == 2 ? 1 : c)) * STRIDE];
+                }
+                T An[NC], Bn[NC];
+                ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
+                T Ac[NC], Bc[NC];   // back to natural order
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int pc = c == 1 ? 2 : (c == 2 ? 1 : c);
+                    Ac[c] = An[pc];
+                    Bc[c] = Bn[pc];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) Dy[k][c] = Dy[k + 1][c];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    Dy[4][c] = Ac[c] - Ap[c] + Bp[c];   // jump across row s (valid once s > s_begin)
+                    Ap[c] = Ac[c];
+                    Bp[c] = Bc[c];
+                }
             }
+            // ---- x-faces of output row r ----------------------------------
+            if (out_row && tid < Wc + 5) {
+                const T *row = ring + RG::slot(r) * (NC * STRIDE) + tid;
+                T st[NS][NC];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+                for (int q = 0; q < NS; ++q)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) Dy[k][c] = Dy[k + 1][c];
+                    for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + q];
+                T An[NC], Bn[NC];
+                ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                Dy[4][c] = Ac[c] - Ap[c] + Bp[c];   // jump across row s (valid once s > s_begin)
-                Ap[c] = Ac[c];
-                Bp[c] = Bc[c];
-            }
-        }
-        // ---- x-faces of output row r ----------------------------------
-        if (out_row && tid < Wc + 5) {
-            const T *row = ring + RG::slot(r) * (NC * STRIDE) + tid;
-            T st[NS][NC];
-#pragma unroll
-            for (int q = 0; q < NS; ++q)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + q];
-            T An[NC], Bn[NC];
-            ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                FA[c * NT + tid] = An[c];
-                FB[c * NT + tid] = Bn[c];
+                for (int c = 0; c < NC; ++c) {
+                    FA[c * NT + tid] = An[c];
+                    FB[c * NT + tid] = Bn[c];
+                }
             }
         }
         __syncthreads();
@@ -399,7 +454,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(Sta
         const int strip = (int)(rem / ny);
         const int y0 = (int)(rem - (long)strip * ny);
         const int y1 = (int)min((long long)ny, y0 + (uend - u));
-        stage2d_segment<T, R, NT, 5, VAR>(a, tb, strip, y0, y1, smem, T(0), rmx, rmy, ok, (long)z * nx * ny);
+        stage2d_segment<T, R, NT, 5, VAR, true>(a, tb, strip, y0, y1, smem, T(0), rmx, rmy, ok, (long)z * nx * ny);
         u += y1 - y0;
     }
     if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(a.flags, 1);
