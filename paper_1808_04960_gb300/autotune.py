@@ -66,3 +66,37 @@ def tune_batch(plans, Us, Ss, dt_dev, cache_path=None, candidates=CANDIDATES, st
         with open(cache_path, "w") as f:
             f.writelines(lines)
     return best, timings
+
+
+def _main():
+    """Tune the seeded batch workload (``workloads.batch_instances``) and write its line into a
+    tuning cache: python -m paper_1808_04960_gb300.autotune [--count N] [--cache PATH]."""
+    import argparse
+
+    import torch
+
+    from . import workloads
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=256)
+    ap.add_argument("--cache", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt"))
+    ap.add_argument("--steps", type=int, default=5)
+    args = ap.parse_args()
+    plans, Us, Ss, dts = [], [], [], []
+    for inst in workloads.batch_instances(args.count, seed=5):
+        m = inst["meta"]
+        p = gpweno.Plan(inst["R"], inst["ell_over_dx"], inst["U"].shape[1:], m["dx"], m["bc"], dtype="f32")
+        U = torch.from_numpy(inst["U"]).to("cuda", torch.float32).contiguous()
+        d = torch.zeros(1, dtype=torch.float64, device="cuda")
+        p.cfl_dt(U, 0.4, d)
+        plans.append(p)
+        Us.append(U)
+        Ss.append(p.new_scratch())
+        dts.append(d)
+    best, timings = tune_batch(plans, Us, Ss, torch.cat(dts), args.cache, steps=args.steps, warmup=2)
+    for (block, cps), ms in sorted(timings.items()):
+        print(f"block {block:4d}  ctas/SM {cps}  {ms:8.3f} ms/step")
+    print("best", best, "->", args.cache)
+
+
+if __name__ == "__main__":
+    _main()
