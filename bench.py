@@ -27,7 +27,7 @@ if ROOT not in sys.path:
 
 METRIC = "GP-WENO cell-updates/s per RK stage, FP32 vs FP64, at L1 err vs FP64 oracle"
 UNIT = "cell-updates/s"
-# roofline constants (see DESIGN.md): FP32 FMA lanes x SMs x max SM clock, 2 FLOP per FMA
+# roofline constants: FP32 FMA lanes x SMs x max SM clock, 2 FLOP per FMA
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 

@@ -156,7 +156,7 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
         ncell *= dims->n[d];
     }
     if (ncell > (1L << 31)) {
-        set_error("grid of %ld cells exceeds the 2^31 limit of this build", ncell);
+        set_error("grid of %ld cells exceeds the 2^31-cell limit of the library", ncell);
         return GPWENO_ERR_ARG;
     }
     gpweno_plan p = new (std::nothrow) gpweno_plan_s();

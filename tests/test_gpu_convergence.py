@@ -5,7 +5,7 @@ oracle where the oracle would take minutes):
 * the isentropic vortex of Section 6.2 with l fixed physically reproduces the
   convergence orders of Table 2 (tests/golden/table2_vortex_l1.txt).  The
   paper does not state how its 2D L1 norm is normalised (its coarse-grid values
-  are 40-70x this build's mean absolute density error), so magnitudes are not
+  are 40-70x the mean absolute density error measured here), so magnitudes are not
   compared; at l/Delta < R (R=3 on the 50-cell grid) the GP stencil over-fits and
   the run turns non-physical, so R=3 starts at 100 cells;
 * FP32 bulk arithmetic stays within L1 1e-5 of FP64 over a full vortex period
