@@ -70,6 +70,9 @@ def test_plan_argument_checks_before_device(lib):
         dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2, gamma=1.0),
         dict(R=2, ell_over_dx=12.0, shape=(16, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2,
              eps=1e-40),
+        # an empty dimension, and a grid beyond the 2^31-cell limit
+        dict(R=2, ell_over_dx=12.0, shape=(0, 16), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2),
+        dict(R=2, ell_over_dx=12.0, shape=(65536, 32769), dx=(0.1, 0.1), bc=(("periodic", "periodic"),) * 2),
     ]
     for kw in bad:
         with pytest.raises(gpweno.GpwenoError) as e:
