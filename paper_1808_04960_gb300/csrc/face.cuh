@@ -778,8 +778,57 @@ __device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const Fac
     }
 
     T dq[NC];
+    // FP32 in 1D and 2D: fields in pairs through packed instructions (as in face_rel);
+    // 3D and an odd last field take the scalar loop.
+    constexpr bool kPacked = std::is_same<T, float>::value && NC <= 4;
+    constexpr int kScalarFrom = kPacked ? (NC / 2) * 2 : 0;
+    if constexpr (kPacked) {
 #pragma unroll
-    for (int kk = 0; kk < NC; ++kk) {
+        for (int k0 = 0; k0 + 1 < NC; k0 += 2) {
+            const int k1 = k0 + 1;
+            const float2 lgs = make_float2(f.lrow(k0, JFs), f.lrow(k1, JFs));
+            const float2 lvs = make_float2(f.lrow(k0, JUs), f.lrow(k1, JUs));
+            const float2 fcp = mul2(f2(0.5f), fma2(f2(alpha), lvs, lgs));
+            const float2 fcm = mul2(f2(0.5f), fma2(f2(-alpha), lvs, lgs));
+            float2 p2[NS], m2[NS];
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                p2[j] = make_float2(dp[k0][j], dp[k1][j]);
+                m2[j] = make_float2(dm[k0][j], dm[k1][j]);
+            }
+            float2 pfl[S], pfr[S];
+#pragma unroll
+            for (int h = 0; h < S; ++h) {
+                pfl[h] = (h % 2 == 0 && !MEAN) ? mul2(f2(tb.Psum[h]), fcp) : f2(0.0f);
+                pfr[h] = (h % 2 == 0) ? (MEAN ? mul2(f2(-tb.Psum[h]), m2[R + 1]) : mul2(f2(tb.Psum[h]), fcm))
+                                      : f2(0.0f);
+            }
+            float2 numL = f2(0.0f), denL = f2(0.0f), numR = f2(0.0f), denR = f2(0.0f);
+#pragma unroll
+            for (int m = 0; m <= R; ++m) {
+                const float2 xl = beta_weight2<R, NS>(tb, p2, m, pfl);
+                const float2 xr = beta_weight2<R, NS>(tb, m2, m + 1, pfr);
+                float2 sl = mul2(f2(tb.sl1[m]), fcp), sr = mul2(f2(tb.sr1[m]), fcm);
+#pragma unroll
+                for (int j = 0; j <= R; ++j) {
+                    if (m + j != R) sl = fma2(f2(tb.wl[m][j]), p2[m + j], sl);
+                    if (1 + m + j != R) sr = fma2(f2(tb.wr[m][j]), m2[1 + m + j], sr);
+                }
+                const float2 yl = mul2(f2(tb.gl[m]), xl);
+                const float2 yr = mul2(f2(tb.gr[m]), xr);
+                numL = fma2(yl, sl, numL);
+                denL = add2(denL, yl);
+                numR = fma2(yr, sr, numR);
+                denR = add2(denR, yr);
+            }
+            const float2 q = fma2(numL, make_float2(Num<float>::rcp(denL.x), Num<float>::rcp(denL.y)),
+                                  mul2(numR, make_float2(Num<float>::rcp(denR.x), Num<float>::rcp(denR.y))));
+            dq[k0] = q.x;
+            dq[k1] = q.y;
+        }
+    }
+#pragma unroll
+    for (int kk = kScalarFrom; kk < NC; ++kk) {
         const T lgs = f.lrow(kk, JFs), lvs = f.lrow(kk, JUs);
         const T fcp = T(0.5) * fma(alpha, lvs, lgs), fcm = T(0.5) * fma(-alpha, lvs, lgs);
         // zero mean: shifts g+_s and g-_s; mean: centres cell s (left) and s+1 (right)
