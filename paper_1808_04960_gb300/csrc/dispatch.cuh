@@ -20,6 +20,8 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
         for (int j = 0; j < S; ++j) {
             t.wl[m][j] = (T)p->tab.wl[m * S + j];
             t.wr[m][j] = (T)p->tab.wr[m * S + j];
+            t.gwl[m][j] = (T)p->tab.gwl[m * S + j];
+            t.gwr[m][j] = (T)p->tab.gwr[m * S + j];
         }
     for (int k = 0; k < S; ++k)
         for (int j = 0; j < (R + 2) / 2; ++j) t.Ph[k][j] = (T)p->tab.Ph[k * S + j];
@@ -28,6 +30,8 @@ FaceTables<T, R> make_tables(const gpweno_plan_s *p)
         t.gr[m] = (T)p->tab.gr[m];
         t.sl1[m] = (T)p->tab.sl1[m];
         t.sr1[m] = (T)p->tab.sr1[m];
+        t.gsl1[m] = (T)p->tab.gsl1[m];
+        t.gsr1[m] = (T)p->tab.gsr1[m];
         t.Psum[m] = (T)p->tab.Psum[m];
     }
     t.eps = (T)p->opts.eps;

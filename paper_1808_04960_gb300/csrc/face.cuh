@@ -91,6 +91,10 @@ struct FaceTables {
     T gr[R + 1];          // linear weights, right state
     T sl1[R + 1];         // sum_j wl[m][j] - 1
     T sr1[R + 1];         // sum_j wr[m][j] - 1
+    T gwl[R + 1][R + 1];  // gl[m] wl[m][j]: the weighted sum of Eq. weight_sum takes one FMA per m
+    T gwr[R + 1][R + 1];  // gr[m] wr[m][j]
+    T gsl1[R + 1];        // gl[m] sl1[m]
+    T gsr1[R + 1];        // gr[m] sr1[m]
     T Ph[R + 1][(R + 2) / 2];  // P = v / sqrt(lambda) of K_m(sigma), half form, largest lambda first:
                                // even rows symmetric, odd rows skew (K_m is persymmetric)
     T Psum[R + 1];        // sum_j of each full row of P (zero for the skew rows)
@@ -259,7 +263,7 @@ __device__ __forceinline__ T beta_weight(const FaceTables<T, R> &tb, const T (&d
         ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : d[lo] + d[hi]);
         ms[j] = lo == R ? -d[hi] : (hi == R ? d[lo] : d[lo] - d[hi]);
     }
-    T beta = T(0);
+    T beta = tb.eps;   // (eps + beta), accumulated from eps
 #pragma unroll
     for (int h = 0; h < S; ++h) {
         T dot;
@@ -275,7 +279,7 @@ __device__ __forceinline__ T beta_weight(const FaceTables<T, R> &tb, const T (&d
         }
         beta = fma(dot, dot, beta);
     }
-    const T x = Num<T>::rcp(Num<T>::fmax(Num<T>::add_rn(tb.eps, beta), Num<T>::eps_floor()));
+    const T x = Num<T>::rcp(Num<T>::fmax(beta, Num<T>::eps_floor()));
     return tb.p == 2 ? Num<T>::mul_rn(x, x) : x;
 }
 
@@ -440,7 +444,7 @@ __device__ __forceinline__ float2 beta_weight2(const FaceTables<float, R> &tb, c
         ps[j] = lo == R ? d[hi] : (hi == R ? d[lo] : add2(d[lo], d[hi]));
         ms[j] = lo == R ? mul2(d[hi], f2(-1.0f)) : (hi == R ? d[lo] : sub2(d[lo], d[hi]));
     }
-    float2 beta = f2(0.0f);
+    float2 beta = f2(tb.eps);   // (eps + beta), accumulated from eps
 #pragma unroll
     for (int h = 0; h < S; ++h) {
         float2 dot;
@@ -456,9 +460,8 @@ __device__ __forceinline__ float2 beta_weight2(const FaceTables<float, R> &tb, c
         }
         beta = fma2(dot, dot, beta);
     }
-    const float2 e = add2(f2(tb.eps), beta);
-    const float2 x = make_float2(Num<float>::rcp(fmaxf(e.x, Num<float>::eps_floor())),
-                                 Num<float>::rcp(fmaxf(e.y, Num<float>::eps_floor())));
+    const float2 x = make_float2(Num<float>::rcp(fmaxf(beta.x, Num<float>::eps_floor())),
+                                 Num<float>::rcp(fmaxf(beta.y, Num<float>::eps_floor())));
     return tb.p == 2 ? mul2(x, x) : x;
 }
 
@@ -534,18 +537,17 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
 #pragma unroll
             for (int m = 0; m <= R; ++m) {
                 const float2 xr = beta_weight2<R, NS>(tb, d, m + 1, pfr);
-                float2 sl = mul2(f2(tb.sl1[m]), fc), sr = mul2(f2(tb.sr1[m]), fc);
+                // gamma_m (candidate_m - centre), with gamma folded into the tables
+                float2 sl = mul2(f2(tb.gsl1[m]), fc), sr = mul2(f2(tb.gsr1[m]), fc);
 #pragma unroll
                 for (int j = 0; j <= R; ++j) {
-                    if (m + j != R) sl = fma2(f2(tb.wl[m][j]), d[m + j], sl);
-                    if (1 + m + j != R) sr = fma2(f2(tb.wr[m][j]), d[1 + m + j], sr);
+                    if (m + j != R) sl = fma2(f2(tb.gwl[m][j]), d[m + j], sl);
+                    if (1 + m + j != R) sr = fma2(f2(tb.gwr[m][j]), d[1 + m + j], sr);
                 }
-                const float2 yl = mul2(f2(tb.gl[m]), xl);
-                const float2 yr = mul2(f2(tb.gr[m]), xr);
-                numL = fma2(yl, sl, numL);
-                denL = add2(denL, yl);
-                numR = fma2(yr, sr, numR);
-                denR = add2(denR, yr);
+                numL = fma2(xl, sl, numL);
+                denL = fma2(f2(tb.gl[m]), xl, denL);
+                numR = fma2(xr, sr, numR);
+                denR = fma2(f2(tb.gr[m]), xr, denR);
                 if (m < R) xl = MEAN ? beta_weight2<R, NS>(tb, d, m + 1, pfl) : xr;
             }
             const float2 qL = mul2(numL, make_float2(Num<float>::rcp(denL.x), Num<float>::rcp(denL.y)));
@@ -586,18 +588,16 @@ __device__ __forceinline__ bool face_rel(const T (&st)[2 * R + 2][NC], const Fac
 #pragma unroll
             for (int m = 0; m <= R; ++m) {
                 const T xr = beta_weight<T, R, NS>(tb, d, m + 1, pfr);
-                T sl = tb.sl1[m] * fc, sr = tb.sr1[m] * fc;
+                T sl = tb.gsl1[m] * fc, sr = tb.gsr1[m] * fc;   // gamma_m (candidate_m - centre)
 #pragma unroll
                 for (int j = 0; j <= R; ++j) {
-                    if (m + j != R) sl = fma(tb.wl[m][j], d[m + j], sl);
-                    if (1 + m + j != R) sr = fma(tb.wr[m][j], d[1 + m + j], sr);
+                    if (m + j != R) sl = fma(tb.gwl[m][j], d[m + j], sl);
+                    if (1 + m + j != R) sr = fma(tb.gwr[m][j], d[1 + m + j], sr);
                 }
-                const T yl = Num<T>::mul_rn(tb.gl[m], xl);
-                const T yr = Num<T>::mul_rn(tb.gr[m], xr);
-                numL = fma(yl, sl, numL);
-                denL = Num<T>::add_rn(denL, yl);
-                numR = fma(yr, sr, numR);
-                denR = Num<T>::add_rn(denR, yr);
+                numL = fma(xl, sl, numL);
+                denL = fma(tb.gl[m], xl, denL);
+                numR = fma(xr, sr, numR);
+                denR = fma(tb.gr[m], xr, denR);
                 if (m < R) xl = MEAN ? beta_weight<T, R, NS>(tb, d, m + 1, pfl) : xr;
             }
             dqL[kk] = numL * Num<T>::rcp(denL);              // q_L - L V_s
@@ -808,18 +808,16 @@ __device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const Fac
             for (int m = 0; m <= R; ++m) {
                 const float2 xl = beta_weight2<R, NS>(tb, p2, m, pfl);
                 const float2 xr = beta_weight2<R, NS>(tb, m2, m + 1, pfr);
-                float2 sl = mul2(f2(tb.sl1[m]), fcp), sr = mul2(f2(tb.sr1[m]), fcm);
+                float2 sl = mul2(f2(tb.gsl1[m]), fcp), sr = mul2(f2(tb.gsr1[m]), fcm);
 #pragma unroll
                 for (int j = 0; j <= R; ++j) {
-                    if (m + j != R) sl = fma2(f2(tb.wl[m][j]), p2[m + j], sl);
-                    if (1 + m + j != R) sr = fma2(f2(tb.wr[m][j]), m2[1 + m + j], sr);
+                    if (m + j != R) sl = fma2(f2(tb.gwl[m][j]), p2[m + j], sl);
+                    if (1 + m + j != R) sr = fma2(f2(tb.gwr[m][j]), m2[1 + m + j], sr);
                 }
-                const float2 yl = mul2(f2(tb.gl[m]), xl);
-                const float2 yr = mul2(f2(tb.gr[m]), xr);
-                numL = fma2(yl, sl, numL);
-                denL = add2(denL, yl);
-                numR = fma2(yr, sr, numR);
-                denR = add2(denR, yr);
+                numL = fma2(xl, sl, numL);
+                denL = fma2(f2(tb.gl[m]), xl, denL);
+                numR = fma2(xr, sr, numR);
+                denR = fma2(f2(tb.gr[m]), xr, denR);
             }
             const float2 q = fma2(numL, make_float2(Num<float>::rcp(denL.x), Num<float>::rcp(denL.y)),
                                   mul2(numR, make_float2(Num<float>::rcp(denR.x), Num<float>::rcp(denR.y))));
@@ -843,18 +841,16 @@ __device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const Fac
         for (int m = 0; m <= R; ++m) {
             const T xl = beta_weight<T, R, NS>(tb, dp[kk], m, pfl);
             const T xr = beta_weight<T, R, NS>(tb, dm[kk], m + 1, pfr);
-            T sl = tb.sl1[m] * fcp, sr = tb.sr1[m] * fcm;
+            T sl = tb.gsl1[m] * fcp, sr = tb.gsr1[m] * fcm;
 #pragma unroll
             for (int j = 0; j <= R; ++j) {
-                if (m + j != R) sl = fma(tb.wl[m][j], dp[kk][m + j], sl);
-                if (1 + m + j != R) sr = fma(tb.wr[m][j], dm[kk][1 + m + j], sr);
+                if (m + j != R) sl = fma(tb.gwl[m][j], dp[kk][m + j], sl);
+                if (1 + m + j != R) sr = fma(tb.gwr[m][j], dm[kk][1 + m + j], sr);
             }
-            const T yl = Num<T>::mul_rn(tb.gl[m], xl);
-            const T yr = Num<T>::mul_rn(tb.gr[m], xr);
-            numL = fma(yl, sl, numL);
-            denL = Num<T>::add_rn(denL, yl);
-            numR = fma(yr, sr, numR);
-            denR = Num<T>::add_rn(denR, yr);
+            numL = fma(xl, sl, numL);
+            denL = fma(tb.gl[m], xl, denL);
+            numR = fma(xr, sr, numR);
+            denR = fma(tb.gr[m], xr, denR);
         }
         dq[kk] = fma(numL, Num<T>::rcp(denL), numR * Num<T>::rcp(denR));
     }

@@ -518,6 +518,14 @@ int gp_precompute(int R, double ell, double sigma, GpTables *out, char *err, std
     if (!side_tables(ql, R, -1, out->wr, out->wbig_r, out->gr, &resid_r, nullptr, out->sr1, err, errlen, kind))
         return 2;
     out->cond_estimate = cond;
+    for (int m = 0; m < S; ++m) {
+        for (int j = 0; j < S; ++j) {
+            out->gwl[m * S + j] = out->gl[m] * out->wl[m * S + j];
+            out->gwr[m * S + j] = out->gr[m] * out->wr[m * S + j];
+        }
+        out->gsl1[m] = out->gl[m] * out->sl1[m];
+        out->gsr1[m] = out->gr[m] * out->sr1[m];
+    }
     // double-double carries ~2^-104 relative; demand cond * 2^-104 < 1e-6
     if (cond * 4.93e-32 > 1e-6) {
         std::snprintf(err, errlen, "covariance of R=%d at l/dx=%g has condition ~%.3g, beyond double-double", R, ell,

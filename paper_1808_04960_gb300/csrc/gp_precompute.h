@@ -31,6 +31,9 @@ struct GpTables {
     double Psum[kMaxS];          // sum_j P_kj of each full row, same order as Ph (0 for skew rows)
     double sl1[kMaxS];           // sum_j wl[m][j] - 1, from the double-double weights
     double sr1[kMaxS];           // sum_j wr[m][j] - 1
+    // the same scaled by the linear weights, for the weighted sum of Eq. weight_sum:
+    // gwl[m][j] = gl[m] wl[m][j], gsl1[m] = gl[m] sl1[m] (and right)
+    double gwl[kMaxS * kMaxS], gwr[kMaxS * kMaxS], gsl1[kMaxS], gsr1[kMaxS];
     double ls_residual;          // ||M gamma - w||_2 of the left-state system
     double cond_estimate;        // rough condition estimate of K(l)
 };
