@@ -5,7 +5,7 @@ written from the steps of the scheme (not from the kernel's instruction
 stream): dense characteristic projection L U and back-projection R q, R+2
 smoothness windows per field (Eq. beta-eigen, shared by the two sides of a
 face), 2(R+1) candidate dot products per field (Eq. candidate_interp), the
-nonlinear weights in ratio form (Eq. weights), the Lax-Friedrichs flux, the
+nonlinear weights (Eq. weights), the Lax-Friedrichs flux, the
 correction of Eqs. numFlux_cor / FD-ders, the divergence of Eq. disc_fd and
 the SSP-RK3 stage combination.  An add, multiply, divide, square root or
 comparison counts 1; a fused multiply-add counts 2.
