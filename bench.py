@@ -489,6 +489,35 @@ def run_variants(args, stream):
     return out
 
 
+def _oracle_sample(job):
+    """One oracle run of the bounded sample (a worker of the all-core measurement)."""
+    n, R, steps = job
+    import oracle
+    from paper_1808_04960_gb300 import workloads
+    U0, meta = workloads.isentropic_vortex(n)
+    o = oracle.Oracle(U0.shape[1:], meta["dx"], meta["bc"], R=R, ell_over_dx=12.0)
+    o.run(U0, 0.4 / o.max_rate(U0), steps)
+    return n * n * 3 * steps
+
+
+def oracle_all_cores(n, R, steps):
+    """The same sample on every host core at once: independent oracle processes (spawned, so
+    no CUDA state is inherited), aggregate cell-updates/s over the wall time."""
+    import multiprocessing as mproc
+    cores = os.cpu_count() or 1
+    ctx = mproc.get_context("spawn")
+    try:
+        with ctx.Pool(cores) as pool:
+            pool.map_async(_oracle_sample, [(16, R, 1)] * cores).get(timeout=300)   # start-up, untimed
+            t0 = time.perf_counter()
+            work = sum(pool.map_async(_oracle_sample, [(n, R, steps)] * cores).get(timeout=600))
+            secs = time.perf_counter() - t0
+    except Exception as e:   # the single-thread figure stands on its own
+        return {"unavailable": f"{type(e).__name__}: {e}"}
+    return {"value": work / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent copies of the single-thread sample, {secs:.2f} s wall"}
+
+
 def cpu_baseline(args, dt_full, gpu_compare=True):
     """The FP64 oracle, as it stands, on a bounded sample: the vortex at `--cpu-grid`^2 for
     `--cpu-steps` RK3 steps (single-threaded C).  Also reports the GPU FP32/FP64 error
@@ -507,6 +536,7 @@ def cpu_baseline(args, dt_full, gpu_compare=True):
     out = {"value": n * n * 3 * args.cpu_steps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"vortex {n}x{n}, GP-R{args.R}, {args.cpu_steps} SSP-RK3 steps, FP64 C oracle, "
                      f"1 thread, {secs:.2f} s"}
+    out["all_cores"] = oracle_all_cores(n, args.R, args.cpu_steps)
     if gpu_compare:
         import torch
 
