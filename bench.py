@@ -311,9 +311,9 @@ def run_gpu(args):
         "accuracy": acc,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak,
-                     "traffic": (kernel_traffic(f"stage2d_kernel<float,{R},256> vortex{n}")
+                     "traffic": (kernel_traffic(f"stage2d_kernel<float,{R},128> vortex{n}")
                                  if args.graph and n == 1024 and R == 2 else None),
-                     "kernel": f"stage2d_kernel<float,{R},256>",
+                     "kernel": f"stage2d_kernel<float,{R},128>",
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "flops_per_cell_stage": flops_per_cell_stage(R)},
         "roofline_hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",

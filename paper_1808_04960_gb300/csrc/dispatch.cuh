@@ -9,6 +9,17 @@
 namespace gpweno {
 
 constexpr int kNT2D = 256;
+// Block size of the xy-sweeping kernels (2D stage, 3D plane).  FP32: 128 threads,
+// four CTAs per SM (128 registers each, as 256-thread CTAs two per SM): a strip is
+// at most 123 columns, so every warp of a CTA evaluates faces and the four SM
+// sub-partitions each hold four busy warps.  With 256 threads and strips
+// narrower than 251 columns (205 at nx = 1024) the eighth warp of each CTA idles
+// and its sub-partition carries half the load of the others, while a row takes
+// as long as the busiest sub-partition needs (measured on GB300: +8 % at 1024^2,
+// +6 % at 2048^2, +1 % at 4096^2).  FP64 (255 registers, one 256-thread CTA per
+// SM) keeps 256: 128 measured 4 % slower.
+template <typename T>
+constexpr int kNTxy = sizeof(T) == 4 ? 128 : 256;
 constexpr int kNT1D = 128;
 
 template <typename T, int R>
@@ -158,9 +169,9 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
     StageArgs<T> a = a0;
     const TablesFor<T, R, VAR> tb = make_tables_var<T, R, VAR>(p);
     if (p->dims.ndim == 3) {
-        constexpr int NT = kNT2D;
         // (1) xy-plane kernel: P = -(div_x/dx + div_y/dy)
         {
+            constexpr int NT = kNTxy<T>;
             const size_t smem = stage2d_smem_bytes<T, R, NT, 5>();
             auto kern = plane3d_kernel<T, R, NT, VAR>;
             static int occ = 0;
@@ -186,6 +197,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         }
         // (2) z-marching kernel: L = P - div_z/dz and the stage update
         {
+            constexpr int NT = kNT2D;
             const size_t smem = stagez_smem_bytes<T, R, NT>();
             auto kern = stagez_kernel<T, R, NT, VAR>;
             static int occ = 0;
@@ -202,7 +214,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
             if (e != cudaSuccess) return cuda_fail(e, "stagez kernel launch");
         }
     } else if (p->dims.ndim == 2) {
-        constexpr int NT = kNT2D;
+        constexpr int NT = kNTxy<T>;
         const size_t smem = stage2d_smem_bytes<T, R, NT>();
         auto kern = stage2d_kernel<T, R, NT, VAR>;
         static int occ = 0;   // per instantiation: resident CTAs per SM

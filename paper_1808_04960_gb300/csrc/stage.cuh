@@ -402,7 +402,7 @@ __device__ __forceinline__ long long balanced_start(int b, int grid, long long t
 }
 
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) stage2d_kernel(Sta
 // overwrites cell by cell (each cell reads its own P first), so 3D needs no
 // scratch beyond 2D's.
 template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) plane3d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT) plane3d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);

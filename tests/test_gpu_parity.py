@@ -150,6 +150,21 @@ def test_edge_shapes_f64(shape):
         assert np.abs(out - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), bc
 
 
+@pytest.mark.parametrize("shape", [(9, 123), (6, 124), (5, 246), (4, 247), (130, 3), (3, 370)])
+def test_edge_shapes_f32(shape):
+    """FP32 kernels sweep the plane in strips of at most 123 columns (128-thread blocks): exactly
+    one strip, one column more, two full strips, one more, and narrow grids, against the oracle
+    within FP32 rounding of the RHS."""
+    ny, nx = shape
+    U, meta = perturbed_vortex(nx, ny, seed=ny * 1000 + nx + 7)
+    for bc in ("periodic", "outflow"):
+        m = dict(meta)
+        m["bc"] = ((bc, bc), (bc, bc))
+        ref = oracle.Oracle(U.shape[1:], m["dx"], m["bc"], R=2).rhs(U)
+        out = gpu_rhs(U, m, 2, "f32")
+        assert np.abs(out - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max()), bc
+
+
 def test_uniform_state_zero_rhs():
     U = np.zeros((4, 33, 70))
     U[0], U[1], U[2], U[3] = 1.3, 0.4, -0.7, 3.1
