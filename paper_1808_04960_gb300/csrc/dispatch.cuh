@@ -8,16 +8,17 @@
 
 namespace gpweno {
 
-constexpr int kNT2D = 256;
-// Block size of the xy-sweeping kernels (2D stage, 3D plane).  FP32: 128 threads,
-// four CTAs per SM (128 registers each, as 256-thread CTAs two per SM): a strip is
-// at most 123 columns, so every warp of a CTA evaluates faces and the four SM
-// sub-partitions each hold four busy warps.  With 256 threads and strips
-// narrower than 251 columns (205 at nx = 1024) the eighth warp of each CTA idles
-// and its sub-partition carries half the load of the others, while a row takes
-// as long as the busiest sub-partition needs (measured on GB300: +8 % at 1024^2,
-// +6 % at 2048^2, +1 % at 4096^2).  FP64 (255 registers, one 256-thread CTA per
-// SM) keeps 256: 128 measured 4 % slower.
+// Block size of the 3D z-marching kernel (contiguous runs of 256 xy-columns).
+constexpr int kNTz = 256;
+// Block size of the xy-sweeping kernels (2D stage, 3D plane).  FP32: 128 threads
+// and four CTAs per SM, with the same 128 registers per thread as two 256-thread
+// CTAs.  A strip is then at most 123 columns, so every warp of a CTA evaluates
+// faces and each of the four SM sub-partitions holds four busy warps.  With 256
+// threads and strips narrower than 251 columns (205 at nx = 1024) the eighth warp
+// of each CTA idles.  Its sub-partition then carries half the load of the others,
+// and a row takes as long as the busiest sub-partition needs.  Measured on GB300:
+// +8 % at 1024^2, +6 % at 2048^2, +1 % at 4096^2.  FP64 (255 registers, one
+// 256-thread CTA per SM) keeps 256: 128 threads measured 4 % slower.
 template <typename T>
 constexpr int kNTxy = sizeof(T) == 4 ? 128 : 256;
 constexpr int kNT1D = 128;
@@ -197,7 +198,7 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         }
         // (2) z-marching kernel: L = P - div_z/dz and the stage update
         {
-            constexpr int NT = kNT2D;
+            constexpr int NT = kNTz;
             const size_t smem = stagez_smem_bytes<T, R, NT>();
             auto kern = stagez_kernel<T, R, NT, VAR>;
             static int occ = 0;
