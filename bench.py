@@ -27,8 +27,19 @@ if ROOT not in sys.path:
 
 METRIC = "GP-WENO cell-updates/s per RK stage, FP32 vs FP64, at L1 err vs FP64 oracle"
 UNIT = "cell-updates/s"
-# roofline constants: FP32 FMA lanes x SMs x max SM clock, 2 FLOP per FMA
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# FP32 FMA lanes per SM (Blackwell: 4 sub-partitions x 32); the SM count comes from the device
+# and the maximum SM clock from the measured peaks (2070 MHz on GB300 when absent)
+FP32_LANES = 128
+
+
+def alu_peak_flops():
+    """FP32 ALU peak of the current device: SMs x 128 FMA lanes x 2 FLOP x maximum SM clock;
+    returns (FLOP/s, description)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks, _ = read_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * FP32_LANES * 2 * mhz * 1e6, f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz"
 
 
 def flops_per_cell_stage(R: int, ndim: int = 2) -> float:
@@ -293,7 +304,8 @@ def run_gpu(args):
     r32 = results["f32"]
     kernel_s = r32["kernel_ms"] * 1e-3
     flops = flops_per_cell_stage(R) * cells
-    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    alu_peak_fs, alu_peak_kind = alu_peak_flops()
+    alu_peak = alu_peak_fs / 1e12
     achieved = flops / kernel_s / 1e12
     hbm_ach = hbm_bytes_per_cell_stage(4) * cells / kernel_s / 1e9
     line = {
@@ -314,7 +326,7 @@ def run_gpu(args):
                      "traffic": (kernel_traffic(f"stage2d_kernel<float,{R},128> vortex{n}")
                                  if args.graph and n == 1024 and R == 2 else None),
                      "kernel": f"stage2d_kernel<float,{R},128>",
-                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "peak_kind": alu_peak_kind,
                      "flops_per_cell_stage": flops_per_cell_stage(R)},
         "roofline_hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": hbm_ach / peaks.get("hbm_gbs"), "peak_kind": peak_kind,
@@ -411,7 +423,7 @@ def timed_cfl_run(plan, U, steps, stream, flops_cell, cells, bytes_cell):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    alu_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6
+    alu_peak, _ = alu_peak_flops()
     per_stage_s = ms * 1e-3 / 3
     peaks, _ = read_peaks()
     return {"value": cells * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,

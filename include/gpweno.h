@@ -197,7 +197,10 @@ gpweno_status gpweno_rk3_step(gpweno_plan plan, void *U, void *scratch, double d
  *     contents stay in it (nothing in it needs to start at zero); calls whose
  *     kernels overlap on the GPU (other streams, other host threads) race.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current, and so does the first call after the device's
+ *     context was torn down and re-created (cudaDeviceReset); make such a
+ *     first call before any stream capture.
+ *   - gpweno_last_launch_count() afterwards gives this call's launches (3).
  * U: device state buffer (input and output), dt > 0, stream as elsewhere. */
 gpweno_status gpweno_rk3_step_noalloc(gpweno_plan plan, void *U, double dt, void *stream);
 

@@ -45,19 +45,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "euler_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libeuler_oracle.so")
+_LIB_OPS = os.path.join(_BUILD, "libeuler_oracle_ops.so")
 _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle with the host gcc (plain -O2, no fast-math)."""
+def _compile(target, extra):
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    if not os.path.exists(target) or os.path.getmtime(target) < os.path.getmtime(_SRC):
+        tmp = target + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-ffp-contract=off", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, target)
+    return target
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with the host gcc (plain -O2, no fast-math), and its
+    operation-counting build (-DORACLE_COUNT_OPS) beside it."""
+    if force:
+        for t in (_LIB, _LIB_OPS):
+            if os.path.exists(t):
+                os.utime(t, (0, 0))
+    _compile(_LIB_OPS, ["-DORACLE_COUNT_OPS"])
+    return _compile(_LIB, [])
 
 
 class _Cfg(ctypes.Structure):
@@ -98,6 +109,55 @@ def _load():
             lib.oracle_corrected_flux.restype = ctypes.c_double
             _lib = lib
     return _lib
+
+
+_lib_ops = None
+
+
+def _load_ops():
+    """The operation-counting build: same source and arithmetic, with the tally enabled."""
+    global _lib_ops
+    with _lock:
+        if _lib_ops is None:
+            build()
+            lib = ctypes.CDLL(_LIB_OPS)
+            lib.oracle_rk3_step.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_void_p, ctypes.c_double]
+            lib.oracle_rk3_step.restype = ctypes.c_int
+            lib.oracle_ops.argtypes = [ctypes.c_int]
+            lib.oracle_ops.restype = ctypes.c_ulonglong
+            _lib_ops = lib
+    return _lib_ops
+
+
+def op_count(R=2, ndim=2, n=16, **opts):
+    """Floating-point operations the oracle executes for one SSP-RK3 step (three RHS
+    evaluations and the stage combinations) of a periodic smooth field on an n^ndim grid,
+    counted by the -DORACLE_COUNT_OPS build (see euler_oracle.c for the counting rules)."""
+    from paper_1808_04960_gb300 import workloads
+    shape = (n,) * ndim
+    U, meta = workloads.smooth_field(shape, seed=1)
+    o = Oracle(shape, meta["dx"], meta["bc"], R=R, **opts)
+    lib = _load_ops()
+    lib.oracle_ops(1)
+    U = np.ascontiguousarray(U, dtype=np.float64).copy()
+    if lib.oracle_rk3_step(ctypes.byref(o.cfg), U.ctypes.data_as(ctypes.c_void_p), 1e-4):
+        raise FloatingPointError("non-physical state in the counted step")
+    return int(lib.oracle_ops(1))
+
+
+def ops_per_cell_stage(R=2, ndim=2, **opts):
+    """Operations per cell and RK stage, the leading term of the count: a step on n^ndim
+    cells costs a n^ndim + b n^(ndim-1) (each grid line evaluates 5 faces beyond its n), so two
+    grid sizes give a exactly; a third size checks that form."""
+    ns = (12, 18, 24) if ndim < 3 else (8, 10, 12)
+    cnt = [op_count(R, ndim, n, **opts) for n in ns]
+    # solve for a, b from the first two sizes, check the third
+    (n1, n2, n3), (c1, c2, c3) = ns, cnt
+    d = ndim
+    a = (c2 * n1 ** (d - 1) - c1 * n2 ** (d - 1)) / (n2 ** d * n1 ** (d - 1) - n1 ** d * n2 ** (d - 1))
+    b = (c1 - a * n1 ** d) / n1 ** (d - 1)
+    assert abs(a * n3 ** d + b * n3 ** (d - 1) - c3) < 1e-6 * c3, (ns, cnt)
+    return a / 3.0
 
 
 def _ptr(a: np.ndarray):

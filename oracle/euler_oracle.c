@@ -35,10 +35,34 @@
  *
  * Layout: U is structure-of-arrays [nc][nz][ny][nx], nc = ndim+2 components
  * (rho, rho u_1..rho u_ndim, E), interior cells only, FP64.
+ *
+ * Each quantity is computed once where it belongs: the primitive variables of
+ * a cell once per RHS evaluation, the smoothness indicators of a window once
+ * per face and field (with the zero-mean indicators the two states of a face
+ * share R of their R+1 windows), the corrected flux once per face.
+ *
+ * Operation count.  Built with -DORACLE_COUNT_OPS, the OPS() annotations
+ * tally the floating-point operations this file executes for the FD-Prim
+ * scheme (the paper's algorithm in the order above): add, subtract,
+ * multiply, divide and square root count one each, as does a max or min
+ * that selects a value; sign changes, fabs, copies and validity checks count
+ * nothing; a sum of k terms counts k-1 additions; pow(x, p) counts p-1
+ * multiplications; terms of the eigenvector products whose coefficient is a
+ * structural zero are skipped and a coefficient of +-1 costs no multiply.
+ * oracle_ops() returns the tally (always 0 in the normal build, where OPS()
+ * compiles to nothing).  The HLLC and HLL fluxes count the branch they take;
+ * the FD-Flux and GP-AO paths are not annotated.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef ORACLE_COUNT_OPS
+static unsigned long long g_ops = 0;
+#define OPS(n) (g_ops += (unsigned long long)(n))
+#else
+#define OPS(n) ((void)0)
+#endif
 
 #define OR_MAXR 4
 #define OR_MAXC 5
@@ -96,6 +120,7 @@ static double pressure(const double *u, int nc, double g)
 {
     double ke = 0.0;
     for (int a = 1; a < nc - 1; ++a) ke += u[a] * u[a];
+    OPS(2 * (nc - 2) - 1 + 5);
     return (g - 1.0) * (u[nc - 1] - 0.5 * ke / u[0]);
 }
 
@@ -108,18 +133,19 @@ static void normal_flux(const double *u, int nc, double g, double *f)
     f[1] = u[1] * un + p;
     for (int a = 2; a < nc - 1; ++a) f[a] = u[a] * un;
     f[nc - 1] = un * (u[nc - 1] + p);
+    OPS(1 + 2 + (nc - 3) + 2);
 }
 
-/* Roe average of two conserved states (normal-first ordering): density
- * sqrt(rhoL rhoR), sqrt(rho)-weighted velocity and total enthalpy, and the
- * sound speed c^2 = (gamma-1)(H - |u|^2/2).  roe[0] = rho, roe[1..nv] = u,
- * roe[nv+1] = H, roe[nv+2] = c.  Returns 0 if c^2 <= 0 or a density <= 0. */
-static int roe_average(const double *uL, const double *uR, int nc, double g, double *roe)
+/* Roe average of two conserved states (normal-first ordering) with their
+ * pressures pL, pR: density sqrt(rhoL rhoR), sqrt(rho)-weighted velocity and
+ * total enthalpy, and the sound speed c^2 = (gamma-1)(H - |u|^2/2).
+ * roe[0] = rho, roe[1..nv] = u, roe[nv+1] = H, roe[nv+2] = c.  Returns 0 if
+ * c^2 <= 0 or a density <= 0. */
+static int roe_average(const double *uL, const double *uR, double pL, double pR, int nc, double g, double *roe)
 {
     int nv = nc - 2;
     if (!(uL[0] > 0.0) || !(uR[0] > 0.0)) return 0;
     double sL = sqrt(uL[0]), sR = sqrt(uR[0]);
-    double pL = pressure(uL, nc, g), pR = pressure(uR, nc, g);
     double HL = (uL[nc - 1] + pL) / uL[0], HR = (uR[nc - 1] + pR) / uR[0];
     double q2 = 0.0;
     roe[0] = sL * sR;
@@ -129,6 +155,7 @@ static int roe_average(const double *uL, const double *uR, int nc, double g, dou
     }
     double H = (sL * HL + sR * HR) / (sL + sR);
     double c2 = (g - 1.0) * (H - 0.5 * q2);
+    OPS(2 + 4 + 1 + 9 * nv - 1 + 5 + 4 + 1);
     roe[nv + 1] = H;
     if (!(c2 > 0.0)) return 0;
     roe[nv + 2] = sqrt(c2);
@@ -145,23 +172,41 @@ static int roe_average(const double *uL, const double *uR, int nc, double g, dou
 static void prim_eigensystem(double rho, double c, int nc, double Rm[OR_MAXC][OR_MAXC], double Lm[OR_MAXC][OR_MAXC])
 {
     int E = nc - 1;
+    double an = rho / (2.0 * c), c2 = c * c, ap = 1.0 / (2.0 * c2), ie = 1.0 / c2, cr = c / rho;
+    OPS(7);
     memset(Rm, 0, sizeof(double) * OR_MAXC * OR_MAXC);
     memset(Lm, 0, sizeof(double) * OR_MAXC * OR_MAXC);
-    Lm[0][1] = -rho / (2.0 * c);
-    Lm[0][E] = 1.0 / (2.0 * c * c);
+    Lm[0][1] = -an;
+    Lm[0][E] = ap;
     Lm[1][0] = 1.0;
-    Lm[1][E] = -1.0 / (c * c);
+    Lm[1][E] = -ie;
     for (int t = 2; t < E; ++t) Lm[t][t] = 1.0;
-    Lm[E][1] = rho / (2.0 * c);
-    Lm[E][E] = 1.0 / (2.0 * c * c);
+    Lm[E][1] = an;
+    Lm[E][E] = ap;
     Rm[0][0] = 1.0;
-    Rm[1][0] = -c / rho;
-    Rm[E][0] = c * c;
+    Rm[1][0] = -cr;
+    Rm[E][0] = c2;
     Rm[0][1] = 1.0;
     for (int t = 2; t < E; ++t) Rm[t][t] = 1.0;
     Rm[0][E] = 1.0;
-    Rm[1][E] = c / rho;
-    Rm[E][E] = c * c;
+    Rm[1][E] = cr;
+    Rm[E][E] = c2;
+}
+
+/* row . v over the non-zero entries of a row of an eigenvector matrix (the
+ * zeros are structural; a coefficient of +-1 needs no multiply). */
+static double dot_sparse(const double *row, const double *v, int n)
+{
+    double acc = 0.0;
+    int first = 1;
+    for (int a = 0; a < n; ++a) {
+        if (row[a] == 0.0) continue;
+        acc += row[a] * v[a];
+        OPS((fabs(row[a]) == 1.0 ? 0 : 1) + (first ? 0 : 1));
+        first = 0;
+    }
+    (void)first;
+    return acc;
 }
 
 /* Primitive variables (rho, u..., p) of a conserved state, same ordering. */
@@ -169,6 +214,7 @@ static void to_primitive(const double *u, int nc, double g, double *v)
 {
     v[0] = u[0];
     for (int a = 1; a < nc - 1; ++a) v[a] = u[a] / u[0];
+    OPS(nc - 2);
     v[nc - 1] = pressure(u, nc, g);
 }
 
@@ -181,12 +227,57 @@ static void to_conserved(const double *v, int nc, double g, double *u)
         ke += v[a] * v[a];
     }
     u[nc - 1] = v[nc - 1] / (g - 1.0) + 0.5 * v[0] * ke;
+    OPS(3 * (nc - 2) - 1 + 5);
+}
+
+/* GP smoothness indicator of one sub-stencil window f[0..R] (Eq. gp-smooth):
+ * beta = d^T K^-1 d with d = f - mean, evaluated as d . (K^-1 d); mean = 0 for
+ * the zero-mean GP, the centre value f_i of the stencil with a non-zero mean
+ * (Section 3.3, the variant of Section 7.1). */
+static double beta_window(const oracle_cfg *c, const double *f, double mean)
+{
+    int S = c->R + 1;
+    double d[OR_MAXR + 1], beta = 0.0;
+    for (int a = 0; a < S; ++a) d[a] = c->beta_mean ? f[a] - mean : f[a];
+    if (c->beta_mean) OPS(S);
+    for (int a = 0; a < S; ++a) {
+        double y = 0.0;
+        for (int b = 0; b < S; ++b) y += c->Kinv[a * S + b] * d[b];
+        beta += d[a] * y;
+    }
+    OPS(S * (2 * S - 1) + 2 * S - 1);
+    return beta;
+}
+
+/* Smoothness indicators of the sub-stencils of both states of a face from the
+ * 2R+2 values f[0..2R+1] (cells s-R .. s+1+R): bl[m] of window f[m..m+R]
+ * (left state, stencil of cell s) and br[m] of window f[1+m..1+m+R] (right
+ * state, stencil of cell s+1).  With the zero mean the windows shared by the
+ * two states are evaluated once. */
+static void face_betas(const oracle_cfg *c, const double *f, double *bl, double *br)
+{
+    int R = c->R;
+    if (!c->beta_mean) {
+        double b[OR_MAXR + 2];
+        for (int w = 0; w <= R + 1; ++w) b[w] = beta_window(c, f + w, 0.0);
+        for (int m = 0; m <= R; ++m) {
+            bl[m] = b[m];
+            br[m] = b[m + 1];
+        }
+        return;
+    }
+    for (int m = 0; m <= R; ++m) {
+        bl[m] = beta_window(c, f + m, f[R]);
+        br[m] = beta_window(c, f + 1 + m, f[R + 1]);
+    }
 }
 
 /* GP-WENO prediction at one face centre from 2R+1 values f[0..2R] centred on
- * the cell whose stencil is used; w: (R+1)x(R+1) sub-stencil weights, gam:
- * linear weights.  Sub-stencil m covers f[m..m+R] (Eq. sub-stencil). */
-static double gp_weno(const oracle_cfg *c, const double *f, const double *w, const double *gam)
+ * the cell whose stencil is used and the smoothness indicators beta[m] of its
+ * sub-stencils; w: (R+1)x(R+1) sub-stencil weights, gam: linear weights.
+ * Sub-stencil m covers f[m..m+R] (Eq. sub-stencil). */
+static double gp_weno(const oracle_cfg *c, const double *f, const double *w, const double *gam,
+                      const double *beta)
 {
     int R = c->R, S = R + 1;
     double q[OR_MAXR + 1], wt[OR_MAXR + 1], wsum = 0.0, out = 0.0;
@@ -194,17 +285,12 @@ static double gp_weno(const oracle_cfg *c, const double *f, const double *w, con
         const double *fm = f + m;
         double qm = 0.0;
         for (int j = 0; j < S; ++j) qm += w[m * S + j] * fm[j];              /* Eq. candidate_interp */
-        /* Eq. gp-smooth; with a non-zero mean the data are taken relative to the
-         * centre value f_i of the stencil (Section 3.3, the variant of Section 7.1) */
-        double mean = c->beta_mean ? f[R] : 0.0;
-        double beta = 0.0;
-        for (int a = 0; a < S; ++a)
-            for (int b = 0; b < S; ++b) beta += (fm[a] - mean) * c->Kinv[a * S + b] * (fm[b] - mean);
         q[m] = qm;
-        wt[m] = gam[m] / pow(c->eps + beta, (double)c->p);                     /* Eq. weights */
+        wt[m] = gam[m] / pow(c->eps + beta[m], (double)c->p);                  /* Eq. weights */
         wsum += wt[m];
     }
     for (int m = 0; m < S; ++m) out += (wt[m] / wsum) * q[m];                   /* Eq. weight_sum */
+    OPS(S * (2 * S - 1) + S * (2 + (c->p - 1)) + (S - 1) + 3 * S - 1);
     return out;
 }
 
@@ -285,6 +371,7 @@ static void hllc_flux(const double *uL, const double *uR, int nc, double g, doub
     double fL[OR_MAXC], fR[OR_MAXC];
     normal_flux(uL, nc, g, fL);
     normal_flux(uR, nc, g, fR);
+    OPS(2 + 6 + 6 + 15);
     if (SL >= 0.0) {
         for (int a = 0; a < nc; ++a) F[a] = fL[a];
         return;
@@ -303,6 +390,7 @@ static void hllc_flux(const double *uL, const double *uR, int nc, double g, doub
     for (int a = 2; a < E; ++a) us[a] = chi * uK[a] / rK;
     us[E] = chi * (uK[E] / rK + (Ss - vK) * (Ss + pK / (rK * (SK - vK))));
     for (int a = 0; a < nc; ++a) F[a] = fK[a] + SK * (us[a] - uK[a]);
+    OPS(1 + 4 + 1 + 2 * (nc - 3) + 9 + 3 * nc);
 }
 
 /* HLL flux (Harten, Lax and van Leer's two-wave solver) of two conserved
@@ -319,10 +407,14 @@ static void hll_flux(const double *uL, const double *uR, int nc, double g, doubl
     double fL[OR_MAXC], fR[OR_MAXC];
     normal_flux(uL, nc, g, fL);
     normal_flux(uR, nc, g, fR);
+    OPS(2 + 6 + 6);
     for (int a = 0; a < nc; ++a) {
         if (SL >= 0.0) F[a] = fL[a];
         else if (SR <= 0.0) F[a] = fR[a];
-        else F[a] = (SR * fL[a] - SL * fR[a] + SL * SR * (uR[a] - uL[a])) / (SR - SL);
+        else {
+            F[a] = (SR * fL[a] - SL * fR[a] + SL * SR * (uR[a] - uL[a])) / (SR - SL);
+            OPS(9);
+        }
     }
 }
 
@@ -345,69 +437,90 @@ static void gather_stencil(const oracle_cfg *c, const double *U, int d, int s, c
     }
 }
 
-/* Face flux F between cells s and s+1 along dimension d, at transverse
- * position (t1, t2) meaning the other two cell indices in natural order.
- * Writes nc values (natural component order).  Returns 0 on a non-physical
- * state. */
-static int face_flux(const oracle_cfg *c, const double *U, int d, int s, const int cell[3], double *Fout,
+/* Primitive variables of the same stencil (from the primitive array V of the
+ * whole grid, same layout as U). */
+static void gather_prim(const oracle_cfg *c, const double *V, int d, int s, const int cell[3], const int perm[OR_MAXC],
+                        double vs[OR_MAXS][OR_MAXC])
+{
+    int nc = c->ndim + 2, R = c->R, ns = 2 * R + 2;
+    long N = ncells(c);
+    for (int q = 0; q < ns; ++q) {
+        int idx[3] = { cell[0], cell[1], cell[2] };
+        idx[d] = map_index(c, d, s - R + q);
+        long l = lin(c, idx[0], idx[1], idx[2]);
+        for (int a = 0; a < nc; ++a) vs[q][a] = V[(long)perm[a] * N + l];
+    }
+}
+
+/* Normal flux of a state from its primitive (v) and conserved (u) forms,
+ * normal-first ordering (Eq. euler). */
+static void flux_prim(const double *v, const double *u, int nc, double *f)
+{
+    double un = v[1], p = v[nc - 1];
+    f[0] = u[1];
+    f[1] = u[1] * un + p;
+    for (int a = 2; a < nc - 1; ++a) f[a] = u[a] * un;
+    f[nc - 1] = un * (u[nc - 1] + p);
+    OPS(2 + (nc - 3) + 2);
+}
+
+/* Face flux F between stencil cells R and R+1 of the conserved stencil st and
+ * its primitive variables vs (2R+2 cells, normal-first).  Writes nc values
+ * (normal-first order) and, if asked, the Riemann states.  Returns 0 on a
+ * non-physical state. */
+static int face_flux(const oracle_cfg *c, double st[OR_MAXS][OR_MAXC], double vs[OR_MAXS][OR_MAXC], double *Fn,
                      double *uLout, double *uRout)
 {
     int nc = c->ndim + 2, R = c->R, ns = 2 * R + 2;
-    int perm[OR_MAXC];
-    double st[OR_MAXS][OR_MAXC];           /* stencil, normal-first, conserved */
-    gather_stencil(c, U, d, s, cell, perm, st);
     double roe[OR_MAXC + 1];
-    if (!roe_average(st[R], st[R + 1], nc, c->gamma, roe)) return 0;
+    if (!roe_average(st[R], st[R + 1], vs[R][nc - 1], vs[R + 1][nc - 1], nc, c->gamma, roe)) return 0;
     double Rm[OR_MAXC][OR_MAXC], Lm[OR_MAXC][OR_MAXC];
     prim_eigensystem(roe[0], roe[nc], nc, Rm, Lm);
 
     /* characteristic projection of the primitive variables of every stencil cell */
     double ch[OR_MAXC][OR_MAXS];
-    for (int q = 0; q < ns; ++q) {
-        double v[OR_MAXC];
-        to_primitive(st[q], nc, c->gamma, v);
-        for (int f = 0; f < nc; ++f) {
-            double acc = 0.0;
-            for (int a = 0; a < nc; ++a) acc += Lm[f][a] * v[a];
-            ch[f][q] = acc;
-        }
-    }
+    for (int q = 0; q < ns; ++q)
+        for (int f = 0; f < nc; ++f) ch[f][q] = dot_sparse(Lm[f], vs[q], nc);
     double wL[OR_MAXC], wR[OR_MAXC];
     for (int f = 0; f < nc; ++f) {
         /* cells s-R..s+R at x* = +1/2; cells s+1-R..s+1+R at x* = -1/2 */
-        wL[f] = c->ao ? gp_ao(c, &ch[f][0], c->ao_l) : gp_weno(c, &ch[f][0], c->wl, c->gl);
-        wR[f] = c->ao ? gp_ao(c, &ch[f][1], c->ao_r) : gp_weno(c, &ch[f][1], c->wr, c->gr);
+        if (c->ao) {
+            wL[f] = gp_ao(c, &ch[f][0], c->ao_l);
+            wR[f] = gp_ao(c, &ch[f][1], c->ao_r);
+        } else {
+            double bl[OR_MAXR + 1], br[OR_MAXR + 1];
+            face_betas(c, ch[f], bl, br);
+            wL[f] = gp_weno(c, &ch[f][0], c->wl, c->gl, bl);
+            wR[f] = gp_weno(c, &ch[f][1], c->wr, c->gr, br);
+        }
     }
+    /* back to primitive states with the right eigenvectors */
     double vL[OR_MAXC], vR[OR_MAXC], uL[OR_MAXC], uR[OR_MAXC];
     for (int a = 0; a < nc; ++a) {
-        double l = 0.0, r = 0.0;
-        for (int f = 0; f < nc; ++f) { l += Rm[a][f] * wL[f]; r += Rm[a][f] * wR[f]; }
-        vL[a] = l; vR[a] = r;
+        vL[a] = dot_sparse(Rm[a], wL, nc);
+        vR[a] = dot_sparse(Rm[a], wR, nc);
     }
     if (!(vL[0] > 0.0) || !(vR[0] > 0.0) || !(vL[nc - 1] > 0.0) || !(vR[nc - 1] > 0.0)) return 0;
     to_conserved(vL, nc, c->gamma, uL);
     to_conserved(vR, nc, c->gamma, uR);
-    double pL = pressure(uL, nc, c->gamma), pR = pressure(uR, nc, c->gamma);
-    if (!(uL[0] > 0.0) || !(uR[0] > 0.0) || !(pL > 0.0) || !(pR > 0.0)) return 0;
-    double Fn[OR_MAXC];
     if (c->flux == 1) {
         hllc_flux(uL, uR, nc, c->gamma, roe[1], roe[nc], Fn);
     } else if (c->flux == 2) {
         hll_flux(uL, uR, nc, c->gamma, roe[1], roe[nc], Fn);
     } else {
-        double cL = sqrt(c->gamma * pL / uL[0]), cR = sqrt(c->gamma * pR / uR[0]);
-        double aL = fabs(uL[1] / uL[0]) + cL, aR = fabs(uR[1] / uR[0]) + cR;
+        /* local Lax-Friedrichs: alpha = max(|u_n| + c) over the two states */
+        double cL = sqrt(c->gamma * vL[nc - 1] / vL[0]), cR = sqrt(c->gamma * vR[nc - 1] / vR[0]);
+        double aL = fabs(vL[1]) + cL, aR = fabs(vR[1]) + cR;
         double alpha = aL > aR ? aL : aR;
+        double ha = 0.5 * alpha;
         double fL[OR_MAXC], fR[OR_MAXC];
-        normal_flux(uL, nc, c->gamma, fL);
-        normal_flux(uR, nc, c->gamma, fR);
-        for (int a = 0; a < nc; ++a) Fn[a] = 0.5 * (fL[a] + fR[a]) - 0.5 * alpha * (uR[a] - uL[a]);
+        flux_prim(vL, uL, nc, fL);
+        flux_prim(vR, uR, nc, fR);
+        for (int a = 0; a < nc; ++a) Fn[a] = 0.5 * (fL[a] + fR[a]) - ha * (uR[a] - uL[a]);
+        OPS(2 * 4 + 1 + 1 + 5 * nc);
     }
-    for (int a = 0; a < nc; ++a) {
-        Fout[perm[a]] = Fn[a];
-        if (uLout) uLout[perm[a]] = uL[a];
-        if (uRout) uRout[perm[a]] = uR[a];
-    }
+    if (uLout) memcpy(uLout, uL, sizeof(double) * nc);
+    if (uRout) memcpy(uRout, uR, sizeof(double) * nc);
     return 1;
 }
 
@@ -482,7 +595,9 @@ static int face_flux_fd(const oracle_cfg *c, const double *U, int d, int s, cons
     double st[OR_MAXS][OR_MAXC];
     gather_stencil(c, U, d, s, cell, perm, st);
     double roe[OR_MAXC + 1];
-    if (!roe_average(st[R], st[R + 1], nc, c->gamma, roe)) return 0;
+    if (!roe_average(st[R], st[R + 1], pressure(st[R], nc, c->gamma), pressure(st[R + 1], nc, c->gamma), nc,
+                     c->gamma, roe))
+        return 0;
     double Rc[OR_MAXC][OR_MAXC], Lc[OR_MAXC][OR_MAXC];
     if (!cons_eigensystem(&roe[1], roe[nc - 1], roe[nc], nc, Rc, Lc)) return 0;
     double alpha = 0.0;
@@ -507,9 +622,19 @@ static int face_flux_fd(const oracle_cfg *c, const double *U, int d, int s, cons
         }
     }
     double hat[OR_MAXC];
-    for (int f = 0; f < nc; ++f)
-        hat[f] = c->ao ? gp_ao(c, &gp[f][0], c->ao_l) + gp_ao(c, &gm[f][1], c->ao_r)
-                       : gp_weno(c, &gp[f][0], c->wl, c->gl) + gp_weno(c, &gm[f][1], c->wr, c->gr);
+    for (int f = 0; f < nc; ++f) {
+        if (c->ao) {
+            hat[f] = gp_ao(c, &gp[f][0], c->ao_l) + gp_ao(c, &gm[f][1], c->ao_r);
+            continue;
+        }
+        /* the two split parts have separate data, hence separate windows */
+        double bl[OR_MAXR + 1], br[OR_MAXR + 1];
+        for (int m = 0; m <= R; ++m) {
+            bl[m] = beta_window(c, &gp[f][m], gp[f][R]);
+            br[m] = beta_window(c, &gm[f][1 + m], gm[f][R + 1]);
+        }
+        hat[f] = gp_weno(c, &gp[f][0], c->wl, c->gl, bl) + gp_weno(c, &gm[f][1], c->wr, c->gr, br);
+    }
     for (int a = 0; a < nc; ++a) {
         double acc = 0.0;
         for (int f = 0; f < nc; ++f) acc += Rc[a][f] * hat[f];
@@ -526,12 +651,15 @@ static double corrected_flux(const double *F5)
     const double A2 = -1.0 / 24.0, A4 = 3.0 / 640.0;
     double D2 = F5[1] - 2.0 * F5[2] + F5[3];
     double D4 = F5[0] - 4.0 * F5[1] + 6.0 * F5[2] - 4.0 * F5[3] + F5[4];
+    OPS(3 + 7 + 4);
     return F5[2] + A2 * D2 + A4 * D4;
 }
 
 double oracle_corrected_flux(const double *F5) { return corrected_flux(F5); }
 
 /* dUdt = L(U), Eq. disc_fd with the corrected fluxes of Eq. numFlux_cor.
+ * Per direction and grid line: the face fluxes F_{s+1/2}, s = -3 .. n+1, then
+ * the corrected flux of each face s = -1 .. n-1 once, then the differences.
  * Returns 0 on success, 1 if any non-physical state was met. */
 int oracle_rhs(const oracle_cfg *c, const double *U, double *dUdt)
 {
@@ -539,39 +667,64 @@ int oracle_rhs(const oracle_cfg *c, const double *U, double *dUdt)
     long N = ncells(c);
     int bad = 0;
     memset(dUdt, 0, sizeof(double) * nc * N);
+    /* FD-Prim: the primitive variables of every cell, once per evaluation */
+    double *V = NULL;
+    if (c->scheme == 0) {
+        V = (double *)malloc(sizeof(double) * nc * N);
+        for (long l = 0; l < N; ++l) {
+            double u[OR_MAXC], v[OR_MAXC];
+            for (int a = 0; a < nc; ++a) u[a] = U[(long)a * N + l];
+            to_primitive(u, nc, c->gamma, v);
+            for (int a = 0; a < nc; ++a) V[(long)a * N + l] = v[a];
+        }
+    }
     for (int d = 0; d < c->ndim; ++d) {
         int n = c->n[d];
         int nf = n + 5;                     /* faces s = -3 .. n+1 */
         double *F = (double *)malloc(sizeof(double) * nf * nc);
+        double *Fh = (double *)malloc(sizeof(double) * (n + 1) * nc);   /* corrected, faces s = -1 .. n-1 */
         int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
         for (int b = 0; b < c->n[t2]; ++b)
             for (int a = 0; a < c->n[t1]; ++a) {
                 int cell[3];
                 cell[t1] = a; cell[t2] = b; cell[d] = 0;
-                for (int s = -3; s <= n + 1; ++s)
-                    if (!(c->scheme == 1 ? face_flux_fd(c, U, d, s, cell, &F[(s + 3) * nc])
-                                         : face_flux(c, U, d, s, cell, &F[(s + 3) * nc], NULL, NULL))) {
+                for (int s = -3; s <= n + 1; ++s) {
+                    double *Fs = &F[(s + 3) * nc];
+                    int ok;
+                    if (c->scheme == 1) {
+                        ok = face_flux_fd(c, U, d, s, cell, Fs);
+                    } else {
+                        int perm[OR_MAXC];
+                        double st[OR_MAXS][OR_MAXC], vs[OR_MAXS][OR_MAXC], Fn[OR_MAXC];
+                        gather_stencil(c, U, d, s, cell, perm, st);
+                        gather_prim(c, V, d, s, cell, perm, vs);
+                        ok = face_flux(c, st, vs, Fn, NULL, NULL);
+                        for (int q = 0; q < nc; ++q) Fs[perm[q]] = Fn[q];
+                    }
+                    if (!ok) {
                         bad = 1;
-                        for (int q = 0; q < nc; ++q) F[(s + 3) * nc + q] = NAN;
+                        for (int q = 0; q < nc; ++q) Fs[q] = NAN;
+                    }
+                }
+                for (int t = -1; t <= n - 1; ++t)
+                    for (int q = 0; q < nc; ++q) {
+                        double F5[5];   /* faces t-2 .. t+2; F index of face s is s+3 */
+                        for (int e = 0; e < 5; ++e) F5[e] = F[(t + 1 + e) * nc + q];
+                        /* FD-Flux: the reconstructed flux is the numerical flux (Eq. design) */
+                        Fh[(t + 1) * nc + q] = c->scheme == 1 ? F5[2] : corrected_flux(F5);
                     }
                 for (int i = 0; i < n; ++i) {
                     cell[d] = i;
                     long l = lin(c, cell[0], cell[1], cell[2]);
-                    for (int q = 0; q < nc; ++q) {
-                        double fh[2];
-                        for (int side = 0; side < 2; ++side) {
-                            int s = i - 1 + side;   /* face s+1/2; F index of face t is t+3 */
-                            double F5[5];
-                            for (int e = 0; e < 5; ++e) F5[e] = F[(s + 1 + e) * nc + q];
-                            /* FD-Flux: the reconstructed flux is the numerical flux (Eq. design) */
-                            fh[side] = c->scheme == 1 ? F5[2] : corrected_flux(F5);
-                        }
-                        dUdt[(long)q * N + l] -= (fh[1] - fh[0]) / c->dx[d];
-                    }
+                    for (int q = 0; q < nc; ++q)
+                        dUdt[(long)q * N + l] -= (Fh[(i + 1) * nc + q] - Fh[i * nc + q]) / c->dx[d];
+                    OPS(3 * nc);
                 }
             }
         free(F);
+        free(Fh);
     }
+    free(V);
     return bad;
 }
 
@@ -591,6 +744,7 @@ int oracle_rk3_step(const oracle_cfg *c, double *U, double dt)
     for (long i = 0; i < M; ++i) U2[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * L[i]);
     bad |= oracle_rhs(c, U2, L);
     for (long i = 0; i < M; ++i) U[i] = U[i] / 3.0 + 2.0 / 3.0 * (U2[i] + dt * L[i]);
+    OPS(M * (2 + 5 + 5));
     free(L); free(U1); free(U2);
     return bad;
 }
@@ -633,8 +787,8 @@ void oracle_hll(int nc, double g, const double *uL, const double *uR, double uro
  * natural order with the normal direction d.  Outputs uL, uR, F (nc each). */
 int oracle_face(const oracle_cfg *c, int d, const double *st, double *uL, double *uR, double *F)
 {
-    /* Build a scratch grid of 2R+2 cells along d (others = 1) and reuse
-     * face_flux on it so the unit test exercises the same code. */
+    /* Build a scratch grid of 2R+2 cells along d (others = 1) and gather the
+     * stencil from it as oracle_rhs does, so the unit test exercises the same code. */
     oracle_cfg g = *c;
     int ns = 2 * c->R + 2, nc = c->ndim + 2;
     for (int a = 0; a < 3; ++a) { g.n[a] = 1; g.bc_lo[a] = g.bc_hi[a] = 1; }
@@ -642,8 +796,17 @@ int oracle_face(const oracle_cfg *c, int d, const double *st, double *uL, double
     double *U = (double *)malloc(sizeof(double) * ns * nc);
     for (int q = 0; q < ns; ++q)
         for (int a = 0; a < nc; ++a) U[(long)a * ns + q] = st[q * nc + a];
-    int cell[3] = { 0, 0, 0 };
-    int ok = face_flux(&g, U, d, c->R, cell, F, uL, uR);
+    int cell[3] = { 0, 0, 0 }, perm[OR_MAXC];
+    double gs[OR_MAXS][OR_MAXC], vs[OR_MAXS][OR_MAXC], Fn[OR_MAXC], uLn[OR_MAXC], uRn[OR_MAXC];
+    gather_stencil(&g, U, d, c->R, cell, perm, gs);
+    for (int q = 0; q < ns; ++q) to_primitive(gs[q], nc, c->gamma, vs[q]);
+    int ok = face_flux(&g, gs, vs, Fn, uLn, uRn);
+    if (ok)
+        for (int a = 0; a < nc; ++a) {
+            F[perm[a]] = Fn[a];
+            uL[perm[a]] = uLn[a];
+            uR[perm[a]] = uRn[a];
+        }
     free(U);
     return ok;
 }
@@ -653,7 +816,7 @@ int oracle_face(const oracle_cfg *c, int d, const double *st, double *uL, double
 int oracle_roe(int nc, double g, const double *uL, const double *uR, double *roe, double *Rout, double *Lout)
 {
     double Rm[OR_MAXC][OR_MAXC], Lm[OR_MAXC][OR_MAXC];
-    if (!roe_average(uL, uR, nc, g, roe)) return 0;
+    if (!roe_average(uL, uR, pressure(uL, nc, g), pressure(uR, nc, g), nc, g, roe)) return 0;
     prim_eigensystem(roe[0], roe[nc], nc, Rm, Lm);
     for (int a = 0; a < nc; ++a)
         for (int b = 0; b < nc; ++b) { Rout[a * nc + b] = Rm[a][b]; Lout[a * nc + b] = Lm[a][b]; }
@@ -664,5 +827,21 @@ int oracle_roe(int nc, double g, const double *uL, const double *uR, double *roe
 double oracle_gp_weno(const oracle_cfg *c, const double *f, int right)
 {
     if (c->ao) return gp_ao(c, f, right ? c->ao_r : c->ao_l);
-    return right ? gp_weno(c, f, c->wr, c->gr) : gp_weno(c, f, c->wl, c->gl);
+    double beta[OR_MAXR + 1];
+    for (int m = 0; m <= c->R; ++m) beta[m] = beta_window(c, f + m, f[c->R]);
+    return right ? gp_weno(c, f, c->wr, c->gr, beta) : gp_weno(c, f, c->wl, c->gl, beta);
+}
+
+/* The operation tally of a build with -DORACLE_COUNT_OPS (0 otherwise); reset
+ * it to zero if asked. */
+unsigned long long oracle_ops(int reset)
+{
+#ifdef ORACLE_COUNT_OPS
+    unsigned long long v = g_ops;
+    if (reset) g_ops = 0;
+    return v;
+#else
+    (void)reset;
+    return 0;
+#endif
 }

@@ -29,6 +29,8 @@ gpweno_status cuda_fail(cudaError_t e, const char *what)
 
 void count_launch(int n) { g_launches += n; }
 
+void reset_launch_count() { g_launches = 0; }
+
 __global__ void dt_from_rate_kernel(unsigned long long *rate, int ndim, double cfl, double *dt_dev)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {

@@ -19,9 +19,12 @@
 //   - every call shares the one array per device, so two calls whose kernels
 //     overlap on the GPU (different streams, or different host threads on the
 //     same device) race and corrupt each other's stages;
-//   - the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture begins.
+//   - the first call on a device (and the first after that device's primary
+//     context was torn down, e.g. by cudaDeviceReset) looks up the array's
+//     device address (cudaGetSymbolAddress) with that device current; make
+//     that first call before any stream capture begins.
+#include <cuda.h>
+
 #include <cstdint>
 #include <mutex>
 
@@ -38,9 +41,38 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_mutex;
+// Per device: the context the address was looked up in, and the address.  An
+// address belongs to one context: after the device's primary context is torn
+// down (cudaDeviceReset) and re-created, the array has a new address, so the
+// cache is keyed on the current context as well as the device.
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device (looked up once per device).
+// The driver's cuCtxGetCurrent through the runtime (no link against libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+gpweno_status current_context(CUcontext *ctx)
+{
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void *sym = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &sym, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !sym)
+            return cuda_fail(e == cudaSuccess ? cudaErrorSymbolNotFound : e,
+                             "gpweno_rk3_step_noalloc: driver entry point cuCtxGetCurrent");
+        fn = reinterpret_cast<CtxGetCurrentFn>(sym);
+    }
+    *ctx = nullptr;
+    if (fn(ctx) != CUDA_SUCCESS || !*ctx) {
+        set_error("gpweno_rk3_step_noalloc: no current CUDA context");
+        return GPWENO_ERR_CUDA;
+    }
+    return GPWENO_OK;
+}
+
+// Device address of the array on the current device, looked up once per
+// device and context.
 gpweno_status static_scratch_address(int device, void **out)
 {
     if (device < 0 || device >= kMaxDevices) {
@@ -48,13 +80,17 @@ gpweno_status static_scratch_address(int device, void **out)
         return GPWENO_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[device]) {
+    CUcontext ctx = nullptr;
+    gpweno_status s = current_context(&ctx);
+    if (s != GPWENO_OK) return s;
+    if (!g_scratch_addr[device] || g_scratch_ctx[device] != ctx) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
         if (e != cudaSuccess || ptr == nullptr)
             return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
                              "gpweno_rk3_step_noalloc: cudaGetSymbolAddress of the static scratch");
         g_scratch_addr[device] = ptr;
+        g_scratch_ctx[device] = ctx;
     }
     *out = g_scratch_addr[device];
     return GPWENO_OK;
@@ -67,6 +103,7 @@ using namespace gpweno;
 
 extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double dt, void *stream)
 {
+    reset_launch_count();
     if (!p || p->is_batch || !U) {
         set_error("gpweno_rk3_step_noalloc: invalid argument");
         return GPWENO_ERR_ARG;

@@ -53,6 +53,7 @@ namespace gpweno {
 void set_error(const char *fmt, ...);
 gpweno_status cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n);
+void reset_launch_count();
 
 // One stage launch (see StageArgs in stage.cuh for the meaning of each buffer).
 struct StageIO {

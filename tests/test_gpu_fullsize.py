@@ -88,13 +88,20 @@ def gpu_step(U0, meta, R, dtype, cfl=0.4):
     return U.double().cpu().numpy(), dt, float(dt_dev.item())
 
 
+def report(name, dtype, emax, emean):
+    """Measured errors on one line (shown with pytest -s), for the record beside the bounds."""
+    print(f"\nFULLSIZE {name} {dtype} linf={emax:.3e} l1={emean:.3e}")
+
+
 def test_vortex_1024_full_size():
+    """Smooth run: FP64 within 1e-10 L-inf of the oracle; FP32 within 1e-5 L1 and 8e-6 L-inf."""
     U0, meta = W.isentropic_vortex(1024)
     blocks = [(0, 0), (500, 500), (512, 100), (1000, 1008), (250, 760)]
-    for dtype, tol in (("f64", 1e-10), ("f32", 2e-6)):
+    for dtype, tol_max, tol_mean in (("f64", 1e-10, 1e-10), ("f32", 8e-6, 1e-5)):
         out, dt, _ = gpu_step(U0, meta, 2, dtype)
-        emax, _ = sampled_parity(U0, meta, 2, out, dt, blocks, 16)
-        assert emax <= tol * 4.0, (dtype, emax)
+        emax, emean = sampled_parity(U0, meta, 2, out, dt, blocks, 16)
+        report("vortex1024", dtype, emax, emean)
+        assert emax <= tol_max and emean <= tol_mean, (dtype, emax, emean)
 
 
 def test_four_quadrant_4096_full_size():
@@ -102,10 +109,11 @@ def test_four_quadrant_4096_full_size():
     # interfaces at x, y = 0.5 (cell 2048), their crossing, the outflow edges and corners
     blocks = [(2040, 2040), (0, 0), (4080, 4080), (2040, 0), (0, 2040), (4080, 2040), (1000, 2040), (2040, 3000),
               (1500, 700)]
-    for dtype, tol_max, tol_mean in (("f64", 1e-9, 1e-10), ("f32", 2e-5, 1e-6)):
+    for dtype, tol_max, tol_mean in (("f64", 1e-9, 1e-9), ("f32", 2e-4, 1e-6)):
         out, dt, dt_next = gpu_step(U0, meta, 2, dtype)
         emax, emean = sampled_parity(U0, meta, 2, out, dt, blocks, 16)
-        assert emean <= tol_mean and emax <= tol_max * 10, (dtype, emax, emean)
+        report("four_quadrant4096", dtype, emax, emean)
+        assert emean <= tol_mean and emax <= tol_max, (dtype, emax, emean)
         assert dt_next > 0
 
 
@@ -115,4 +123,5 @@ def test_shock_turbulence_512_full_size():
     for dtype, tol_mean in (("f32", 1e-5),):
         out, dt, _ = gpu_step(U0, meta, 3, dtype)
         emax, emean = sampled_parity(U0, meta, 3, out, dt, blocks, 8)
+        report("shock_turbulence512", dtype, emax, emean)
         assert emean <= tol_mean, (dtype, emax, emean)

@@ -129,3 +129,61 @@ def test_large_ell_conditioning_handled():
     t48 = gp_tables.tables(3, 48.0, 3.0, 0.5)
     err48 = np.abs(t48["w_big"] - lag).max()
     assert 3.5 < err48 / err96 < 4.5
+
+
+def _mp_gp_linear_weights(R, ell, xs="0.5", dps=60):
+    """Linear weights gamma of Eq. gamm-system at l/Delta = ell, computed here from the
+    definitions with mpmath (LU solves for w and w_m, Householder-QR least squares for gamma)
+    -- a different algorithm and arithmetic from the oracle's decimal normal equations."""
+    import mpmath as mp
+    with mp.workdps(dps):
+        ell = mp.mpf(ell)
+        xs = mp.mpf(xs)
+        k = lambda a, b: mp.e ** (-(a - b) ** 2 / (2 * ell * ell))
+        pts = list(range(-R, R + 1))
+        K = mp.matrix([[k(a, b) for b in pts] for a in pts])
+        w = mp.lu_solve(K, mp.matrix([k(xs, b) for b in pts]))
+        M = mp.zeros(2 * R + 1, R + 1)
+        for m in range(R + 1):
+            sub = pts[m:m + R + 1]
+            Km = mp.matrix([[k(a, b) for b in sub] for a in sub])
+            wm = mp.lu_solve(Km, mp.matrix([k(xs, b) for b in sub]))
+            for j in range(R + 1):
+                M[m + j, m] = wm[j]
+        gam, res = mp.qr_solve(M, w)
+        return [float(gam[m]) for m in range(R + 1)], float(mp.fsum(gam)), float(res)
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_linear_weights_at_ell_12_independent(R):
+    """gamma at l/Delta = 12 (the operating point) to 1e-10 against the mpmath computation
+    above, and not renormalised: sum(gamma) keeps its least-squares defect (a renormalised
+    gamma would pass the flat-limit pins but fail here)."""
+    g_mp, sum_mp, res_mp = _mp_gp_linear_weights(R, 12)
+    t = gp_tables.tables(R, 12.0, 3.0, 0.5)
+    np.testing.assert_allclose(t["gamma"], g_mp, rtol=0, atol=1e-10)
+    assert abs(t["gamma"].sum() - sum_mp) < 1e-12
+    assert abs(sum_mp - 1.0) > 1e-9          # the least-squares gamma does not sum to one
+    assert abs(np.linalg.norm(t["M"] @ t["gamma"] - t["w_big"]) - res_mp) < 1e-9 * max(res_mp, 1e-6)
+
+
+def test_linear_weights_r2_worked_values():
+    """R = 2, l/Delta = 12: the worked values (0.063594, 0.620632, 0.315774) of an
+    independent high-precision probe, to 1e-6."""
+    t = gp_tables.tables(2, 12.0, 3.0, 0.5)
+    np.testing.assert_allclose(t["gamma"], [0.063594, 0.620632, 0.315774], rtol=0, atol=1e-6)
+
+
+# eigenvalues of the (R+1)-point smoothness covariance K_m(sigma/Delta = 3), ascending, as
+# printed by an independent probe to three or four significant digits
+SIGMA3_EIGS = {1: [0.0540, 1.946], 2: [0.00395, 0.199, 2.797], 3: [3.89e-4, 0.0213, 0.447, 3.531]}
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_smoothness_covariance_eigenvalues(R):
+    """lambda_h of K_m(sigma) (Eq. beta-eigen) at sigma/Delta = 3 against the worked values,
+    and their sum = trace K_m = R+1 (unit diagonal)."""
+    t = gp_tables.tables(R, 12.0, 3.0, 0.5)
+    lam = np.sort(t["lam_sigma"])
+    np.testing.assert_allclose(lam, SIGMA3_EIGS[R], rtol=3e-3)
+    assert abs(lam.sum() - (R + 1)) < 1e-13

@@ -27,15 +27,22 @@ def _built():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("dtype,shape,tol", [("f64", (96, 130), 1e-10), ("f32", (256, 300), 1e-6),
-                                             ("f64", (300,), 1e-10)])
-def test_noalloc_matches_scratch_step(dtype, shape, tol):
+@pytest.mark.parametrize("dtype,shape,tol,R", [("f64", (96, 130), 1e-10, 2), ("f32", (256, 300), 1e-6, 2),
+                                               ("f64", (300,), 1e-10, 2), ("f32", (32, 32, 32), 1e-6, 3),
+                                               ("f64", (30, 34, 36), 1e-10, 3)])
+def test_noalloc_matches_scratch_step(dtype, shape, tol, R):
+    """Two calls in a row of each step agree; in 3D the x+y part of L passes through the
+    static array's first two stage slots in turn (V1, V2, V1), so 3D is checked too."""
     import torch
     if len(shape) == 1:
         U0, meta = W.sod_1d(shape[0])
+    elif len(shape) == 3:
+        U0, meta = W.shock_turbulence_3d(shape[2], seed=4)
+        if U0.shape[1:] != shape:   # a ragged box: a window of the cubic one (same spacing)
+            U0 = np.ascontiguousarray(U0[:, :shape[0], :shape[1], :shape[2]])
     else:
         U0, meta = W.four_quadrant(shape[1], seed=3, ny=shape[0])
-    plan = gpweno.Plan(2, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
+    plan = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype=dtype)
     tdt = torch.float32 if dtype == "f32" else torch.float64
     Ua = torch.from_numpy(U0).to("cuda", tdt).contiguous()
     Ub = Ua.clone()
@@ -44,6 +51,7 @@ def test_noalloc_matches_scratch_step(dtype, shape, tol):
     for call in range(2):
         plan.rk3_step(Ua, scratch, dt=dt)
         plan.rk3_step_noalloc(Ub, dt)
+        assert gpweno.last_launch_count() == 3   # this call's stage launches only
         torch.cuda.synchronize()
         a, b = Ua.double().cpu().numpy(), Ub.double().cpu().numpy()
         assert np.isfinite(b).all()
