@@ -194,7 +194,12 @@ def run_gpu(args):
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
+    if local == 0:
+        libbuild.build()
+    barrier(ws)
     libbuild.build()
+    if ws > 1:
+        return run_gpu_slabs(args, ws, rank, local)
     n, R = args.grid, args.R
     U0, meta = workloads.isentropic_vortex(n)
     cells = n * n
@@ -294,7 +299,7 @@ def run_gpu(args):
            "d2h_bytes_per_step": nb, "ms_per_step": e2e_ms / args.steps,
            "copies": "pinned host, own stream per direction, double-buffered, overlapped with compute"}
 
-    batch = run_batch(args, stream) if args.batch_count > 0 else None
+    batch = run_batch(args, stream, rank, ws) if args.batch_count > 0 else None
     extra = run_configs(args, stream) if args.configs else None
     variants = run_variants(args, stream) if args.variant_steps > 0 else None
 
@@ -343,60 +348,213 @@ def run_gpu(args):
     return line
 
 
-def run_batch(args, stream):
-    """Batched workload: `--batch-count` seeded 2D instances (n_x, n_y log-uniform on [64, 1024],
-    R in {1,2,3}, l/dx in {6,12,24}, half four-quadrant, half vortex), FP32, per-instance CFL dt.
-    One persistent launch per RK stage (CUDA graph of the step) against per-instance launches."""
+def run_gpu_slabs(args, ws, rank, local):
+    """N > 1 GPUs: one grid cut into N slabs along y, one slab per GPU, the G = R+3 boundary
+    layers of every stage's input exchanged with the neighbouring slabs over NCCL before the
+    stage (decomp.SlabStepper).  The grid is N periodic images of the single-GPU vortex stacked
+    along y (1024 x 1024 N cells), so every rank steps the single-GPU workload plus the exchange
+    (weak scaling).  FP32, fixed dt; the batch is split over the ranks by instance."""
+    import numpy as np
     import torch
 
-    from paper_1808_04960_gb300 import gpweno, workloads
-    insts = workloads.batch_instances(args.batch_count, seed=5)
-    plans, Us, Ss, dts = [], [], [], []
-    for inst in insts:
-        m = inst["meta"]
-        p = gpweno.Plan(inst["R"], inst["ell_over_dx"], inst["U"].shape[1:], m["dx"], m["bc"], dtype="f32")
-        U = torch.from_numpy(inst["U"]).to("cuda", torch.float32).contiguous()
-        d = torch.zeros(1, dtype=torch.float64, device="cuda")
-        p.cfl_dt(U, 0.4, d)
-        plans.append(p)
-        Us.append(U)
-        Ss.append(p.new_scratch())
-        dts.append(d)
-    dt_dev = torch.cat(dts)
-    dt_host = dt_dev.cpu().tolist()
-    cells = sum(i["nx"] * i["ny"] for i in insts)
-    cache = os.path.join(ROOT, "paper_1808_04960_gb300", "tune_cache.txt")
-    batch = gpweno.BatchPlan(plans, tune_cache=cache)
-    for _ in range(2):
-        batch.rk3_step(Us, Ss, dt_dev, stream=stream)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        batch.rk3_step(Us, Ss, dt_dev)
-    g.replay()
+    from paper_1808_04960_gb300 import decomp, gpweno, workloads
+    n, R = args.grid, args.R
+    U0, meta = workloads.isentropic_vortex(n)
+    cells = n * n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    p64 = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype="f64")
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p64.cfl_dt(torch.from_numpy(U0).to("cuda").contiguous(), 0.4, dt_dev)
+    dt = float(dt_dev.item())
+    slab = decomp.Slab((n * ws, n), meta["bc"], rank, ws, R + 3)
+    assert slab.local_shape == U0.shape[1:]
+    plan = gpweno.Plan(R, 12.0, slab.local_shape, meta["dx"], slab.local_bc, dtype="f32")
+    stepper = decomp.SlabStepper(plan, slab)
+    U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+    for _ in range(args.warmup):
+        stepper.step(U, dt=dt, stream=stream)
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    e[0].record(stream)
-    for _ in range(args.batch_steps):
-        g.replay()
-    e[1].record(stream)
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stepper.step(U, dt=dt, stream=stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        t_list = [a.elapsed_time(b) for a, b in times]
+    barrier(ws)
+    total_ms = max_over_ranks(sum(t_list), ws)
+    nonphys = plan.flags()
+    # end to end: the slab in from pinned host memory, the step, the slab out, every step
+    host = torch.from_numpy(U0.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
+    nb = host.numel() * host.element_size()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        U.copy_(host, non_blocking=True)
+        stepper.step(U, dt=dt, stream=stream)
+        host_out.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    batch = run_batch(args, stream, rank, ws) if args.batch_count > 0 else None
+    if rank != 0:
+        return None
+    kernel_s = total_ms / args.steps / 3.0 * 1e-3
+    alu_peak_fs, alu_peak_kind = alu_peak_flops()
+    achieved = flops_per_cell_stage(R) * cells / kernel_s / 1e12
+    peaks, peak_kind = read_peaks()
+    hbm_ach = hbm_bytes_per_cell_stage(4) * cells / kernel_s / 1e9
+    return {
+        "metric": METRIC, "value": ws * cells * 3 * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"2D isentropic vortex, {ws} periodic images of the {n}x{n} [-5,5]^2 vortex "
+                               f"stacked along y ({n}x{n * ws} cells), GP-R{R}, l=12dx, sigma=3dx, SSP-RK3 fixed "
+                               "dt (CFL 0.4)", "grid": [n, n * ws], "R": R, "ell_over_dx": 12.0,
+                   "sigma_over_dx": 3.0, "dt": dt, "cuda_graph": False,
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": f"slabs{ws}: y-slab per GPU, NCCL halo exchange of G={R + 3} layers "
+                                  "before every stage"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak_fs / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / (alu_peak_fs / 1e12), "traffic": None,
+                     "kernel": f"stage2d_kernel<float,{R},128> (per GPU, step time incl. the exchange)",
+                     "peak_kind": alu_peak_kind, "flops_per_cell_stage": flops_per_cell_stage(R)},
+        "roofline_hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": hbm_ach / peaks.get("hbm_gbs"), "peak_kind": peak_kind},
+        "e2e": {"value": ws * cells * 3 * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
+                "d2h_bytes_per_step": nb, "ms_per_step": e2e_ms / args.steps,
+                "copies": "per rank: its slab in from pinned host memory and out again, every step, one stream"},
+        "batch": batch,
+        "gpu_launches": 6 * args.steps,
+        "nonphysical_flag": nonphys,
+        "clocks": clk.summary(),
+    }
+
+
+def run_batch(args, stream, rank=0, ws=1):
+    """Batched workload: `--batch-count` seeded 2D instances (n_x, n_y log-uniform on [64, 1024],
+    R in {1,2,3}, l/dx in {6,12,24}, half four-quadrant, half vortex), per-instance CFL dt.
+    With N ranks the instances are split over the ranks by estimated cost (no exchange: they are
+    independent), each rank one persistent launch per RK stage for its share.  FP32 under a CUDA
+    graph against per-instance launches and against the FP64 batch; the FP32 states' error
+    against the FP64 batch after the same steps."""
+    import torch
+
+    from paper_1808_04960_gb300 import decomp, gpweno, workloads
+    insts = workloads.batch_instances(args.batch_count, seed=5)
+    costs = [decomp.instance_cost(i["nx"], i["ny"], i["R"]) for i in insts]
+    parts, loads = decomp.shard_instances(costs, ws)
+    mine = [insts[k] for k in parts[rank]]
+    cache = os.path.join(ROOT, "paper_1808_04960_gb300", "tune_cache.txt")
+
+    def build(dtype):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        plans, Us, Ss, dts = [], [], [], []
+        for inst in mine:
+            m = inst["meta"]
+            p = gpweno.Plan(inst["R"], inst["ell_over_dx"], inst["U"].shape[1:], m["dx"], m["bc"], dtype=dtype)
+            U = torch.from_numpy(inst["U"]).to("cuda", tdt).contiguous()
+            plans.append(p)
+            Us.append(U)
+            Ss.append(p.new_scratch())
+        # the same per-instance dt for both precisions: CFL 0.4 of the FP64 initial state
+        for inst in mine:
+            m = inst["meta"]
+            p64 = gpweno.Plan(inst["R"], inst["ell_over_dx"], inst["U"].shape[1:], m["dx"], m["bc"], dtype="f64")
+            d = torch.zeros(1, dtype=torch.float64, device="cuda")
+            p64.cfl_dt(torch.from_numpy(inst["U"]).to("cuda").contiguous(), 0.4, d)
+            dts.append(d)
+        return plans, Us, Ss, torch.cat(dts)
+
+    def timed(batch, Us, Ss, dt_dev, steps, graph=True):
+        for _ in range(2):
+            batch.rk3_step(Us, Ss, dt_dev, stream=stream)
+        g = None
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                batch.rk3_step(Us, Ss, dt_dev)
+            g.replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for _ in range(steps):
+            if g is not None:
+                g.replay()
+            else:
+                batch.rk3_step(Us, Ss, dt_dev, stream=stream)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(e[0].elapsed_time(e[1]), ws) / steps
+
+    plans, Us, Ss, dt_dev = build("f32")
+    cells = sum(i["nx"] * i["ny"] for i in insts)
+    batch = gpweno.BatchPlan(plans, tune_cache=cache)
+    ms_b = timed(batch, Us, Ss, dt_dev, args.batch_steps)
     # per-instance launches (3 per instance per step), no graph
-    e[2].record(stream)
+    dt_host = dt_dev.cpu().tolist()
+    barrier(ws)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
     for _ in range(args.batch_steps):
         for p, U, S, dt in zip(plans, Us, Ss, dt_host):
             p.rk3_step(U, S, dt=dt, stream=stream)
-    e[3].record(stream)
+    e[1].record(stream)
     torch.cuda.synchronize()
-    ms_b = e[0].elapsed_time(e[1]) / args.batch_steps
-    ms_u = e[2].elapsed_time(e[3]) / args.batch_steps
+    ms_u = max_over_ranks(e[0].elapsed_time(e[1]), ws) / args.batch_steps
     nonphys = batch.flags()
     info = batch.info()
-    return {"workload": f"{len(insts)} seeded 2D instances, n_x,n_y log-uniform on [64,1024], R in {{1,2,3}}, "
-                        "l/dx in {6,12,24}, four-quadrant/vortex, FP32, per-instance CFL 0.4",
-            "instances": len(insts), "cells": cells, "steps": args.batch_steps,
-            "value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
-            "unbatched_value": cells * 3 / (ms_u * 1e-3), "unbatched_ms_per_step": ms_u,
-            "speedup_vs_unbatched": ms_u / ms_b, "launches_per_step": 3,
-            "unbatched_launches_per_step": 3 * len(insts), "schedule": info, "nonphysical_flag": nonphys}
+    out = {"workload": f"{len(insts)} seeded 2D instances, n_x,n_y log-uniform on [64,1024], R in {{1,2,3}}, "
+                       "l/dx in {6,12,24}, four-quadrant/vortex, FP32, per-instance CFL 0.4 (fixed dt)",
+           "instances": len(insts), "cells": cells, "steps": args.batch_steps,
+           "value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+           "unbatched_value": cells * 3 / (ms_u * 1e-3), "unbatched_ms_per_step": ms_u,
+           "speedup_vs_unbatched": ms_u / ms_b, "launches_per_step": 3,
+           "unbatched_launches_per_step": 3 * len(insts), "schedule": info, "nonphysical_flag": nonphys,
+           "sharding": {"ranks": ws, "instances_per_rank": [len(p) for p in parts],
+                        "cost_share_max_over_mean": max(loads) / (sum(loads) / ws)}}
+    # FP64 batch from the same initial data: throughput, and the FP32 error against it after the
+    # same number of steps (FP32 states restarted from the initial data; the FP64 GPU path is pinned
+    # to the oracle by the tests)
+    if args.batch_fp64_steps > 0:
+        del batch
+        p64, U64, S64, dt64 = build("f64")
+        b64 = gpweno.BatchPlan(p64, tune_cache=cache)
+        ms_64 = timed(b64, U64, S64, dt64, args.batch_fp64_steps)
+        out["fp64"] = {"value": cells * 3 / (ms_64 * 1e-3), "ms_per_step": ms_64, "steps": args.batch_fp64_steps,
+                       "fp32_over_fp64": ms_64 / ms_b}
+        for U, inst in zip(Us, mine):
+            U.copy_(torch.from_numpy(inst["U"]).to("cuda", torch.float32))
+        for U, inst in zip(U64, mine):
+            U.copy_(torch.from_numpy(inst["U"]).to("cuda", torch.float64))
+        for S in Ss + S64:
+            S.zero_()
+        b32 = gpweno.BatchPlan(plans, tune_cache=cache)
+        k = args.acc_batch_steps
+        for _ in range(k):
+            b32.rk3_step(Us, Ss, dt_dev, stream=stream)
+            b64.rk3_step(U64, S64, dt64, stream=stream)
+        torch.cuda.synchronize()
+        tot, n_el, mx = 0.0, 0, 0.0
+        for a, b in zip(Us, U64):
+            d = (a.double() - b).abs()
+            tot += float(d.sum())
+            n_el += d.numel()
+            mx = max(mx, float(d.max()))
+        out["accuracy"] = {"steps": k, "l1_f32_vs_f64_gpu": tot / max(n_el, 1), "linf_f32_vs_f64_gpu": mx,
+                           "fp64_gpu_vs_oracle": "pinned by tests/test_gpu_batch.py (1e-10)"}
+    return out
 
 
 def timed_cfl_run(plan, U, steps, stream, flops_cell, cells, bytes_cell):
@@ -432,6 +590,42 @@ def timed_cfl_run(plan, U, steps, stream, flops_cell, cells, bytes_cell):
             "hbm_frac": bytes_cell * cells / per_stage_s / (peaks.get("hbm_gbs", 6800.0) * 1e9)}
 
 
+def fp32_vs_fp64(R, U0, meta, steps, stream, **opts):
+    """FP32 and FP64 GPU runs from the same initial data with the same fixed dt (CFL 0.4 of the
+    FP64 initial state): L1 (mean) and L-inf of FP32 - FP64 after `steps` SSP-RK3 steps.  The FP64
+    GPU path itself is pinned to the FP64 oracle by the tests (sampled blocks at full size)."""
+    import torch
+
+    from paper_1808_04960_gb300 import gpweno
+    p64 = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype="f64", **opts)
+    U64 = torch.from_numpy(U0).to("cuda", torch.float64).contiguous()
+    d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p64.cfl_dt(U64, 0.4, d)
+    dt = float(d.item())
+    s64 = p64.new_scratch()
+    for _ in range(steps):
+        p64.rk3_step(U64, s64, dt=dt, stream=stream)
+    del s64
+    p32 = gpweno.Plan(R, 12.0, U0.shape[1:], meta["dx"], meta["bc"], dtype="f32", **opts)
+    U32 = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
+    s32 = p32.new_scratch()
+    for _ in range(steps):
+        p32.rk3_step(U32, s32, dt=dt, stream=stream)
+    del s32
+    torch.cuda.synchronize()
+    l1, linf = 0.0, 0.0
+    for c in range(U32.shape[0]):                     # per component, to bound the extra memory
+        dd = (U32[c].double() - U64[c]).abs()
+        l1 += float(dd.sum())
+        linf = max(linf, float(dd.max()))
+    out = {"steps": steps, "dt": dt, "l1_f32_vs_f64_gpu": l1 / U32.numel(), "linf_f32_vs_f64_gpu": linf,
+           "nonphysical_flag": max(p32.flags(), p64.flags()),
+           "fp64_gpu_vs_oracle": "pinned by the tests (sampled blocks at full size)"}
+    del U32, U64
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_configs(args, stream):
     """The other measured configurations: the 4096^2 seeded four-quadrant Riemann problem (GP-R2,
     l=12dx, CFL 0.4 from the device each step) and the 3D Mach-3 shock into a 32-mode density field
@@ -444,25 +638,33 @@ def run_configs(args, stream):
     U0, m = workloads.four_quadrant(n, seed=3)
     plan = gpweno.Plan(2, 12.0, U0.shape[1:], m["dx"], m["bc"], dtype="f32", cfl=0.4)
     U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
-    del U0
     r = timed_cfl_run(plan, U, args.fq_steps, stream, costmodel.flops_per_cell_stage(2, 2), n * n,
                       hbm_bytes_per_cell_stage(4, 4))
     r["workload"] = f"four-quadrant Riemann problem {n}x{n} on [0,1]^2, seeded states, outflow, GP-R2, l=12dx, " \
                     f"sigma=3dx, SSP-RK3, CFL 0.4 (device dt), FP32"
-    out["four_quadrant"] = r
+    r["flops_per_cell_stage"] = costmodel.flops_per_cell_stage(2, 2)
     del U, plan
+    torch.cuda.empty_cache()
+    if args.acc_config_steps > 0:
+        r["accuracy"] = fp32_vs_fp64(2, U0, m, args.acc_config_steps, stream)
+    out["four_quadrant"] = r
+    del U0
     n3 = args.shock_grid
     if n3 > 0:
         U0, m = workloads.shock_turbulence_3d(n3, seed=4)
         plan = gpweno.Plan(3, 12.0, U0.shape[1:], m["dx"], m["bc"], dtype="f32", cfl=0.4)
         U = torch.from_numpy(U0).to("cuda", torch.float32).contiguous()
-        del U0
         r = timed_cfl_run(plan, U, args.shock_steps, stream, costmodel.flops_per_cell_stage(3, 3), n3 ** 3,
                           hbm_bytes_per_cell_stage(4, 5, 23.0))
         r["workload"] = f"3D Mach-3 shock into a 32-mode seeded density field, {n3}^3, periodic y/z, " \
                         f"zero-gradient x, GP-R3, l=12dx, sigma=3dx, SSP-RK3, CFL 0.4 (device dt), FP32"
-        out["shock_turbulence_3d"] = r
+        r["flops_per_cell_stage"] = costmodel.flops_per_cell_stage(3, 3)
         del U, plan
+        torch.cuda.empty_cache()
+        if args.acc_config_steps > 0:
+            r["accuracy"] = fp32_vs_fp64(3, U0, m, max(1, args.acc_config_steps // 5), stream)
+        out["shock_turbulence_3d"] = r
+        del U0
     torch.cuda.empty_cache()
     return out
 
@@ -493,10 +695,13 @@ def run_variants(args, stream):
         flops = costmodel.flops_per_cell_stage(2, 2, **cm)
         r = timed_cfl_run(plan, U, args.variant_steps, stream, flops, n * n, hbm_bytes_per_cell_stage(4, 4))
         r["flops_per_cell_stage"] = flops
+        r["flops_kind"] = "modelled" if cm.get("scheme") == "fdflux" or cm.get("ao") else "oracle tally"
         base = base or r["value"]
         r["vs_default"] = r["value"] / base
-        out[name] = r
         del U, plan
+        if args.acc_config_steps > 0:
+            r["accuracy"] = fp32_vs_fp64(2, U0, m, args.acc_config_steps, stream, **opts)
+        out[name] = r
     torch.cuda.empty_cache()
     return out
 
@@ -620,6 +825,10 @@ def main():
     ap.add_argument("--dtypes", default="f32,f64", help="comma list; f32 is always first and required")
     ap.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-fp64-steps", type=int, default=3, help="timed steps of the FP64 batch (0: skip)")
+    ap.add_argument("--acc-batch-steps", type=int, default=5, help="steps of the batch FP32-vs-FP64 comparison")
+    ap.add_argument("--acc-config-steps", type=int, default=10,
+                    help="steps of the FP32-vs-FP64 comparison of the 4096^2 and variant runs (3D: a fifth)")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip the four-quadrant 4096^2 and 3D shock-turbulence measurements")
     ap.add_argument("--fq-grid", type=int, default=4096)

@@ -50,13 +50,20 @@ typedef enum {
 } gpweno_status;
 
 typedef enum { GPWENO_F32 = 0, GPWENO_F64 = 1 } gpweno_dtype;
-typedef enum { GPWENO_BC_PERIODIC = 0, GPWENO_BC_OUTFLOW = 1 } gpweno_bc;
+/* Boundary conditions per side of a dimension.  GPWENO_BC_EXTERNAL: the ghost
+ * layers of that side are supplied by the caller in a halo buffer (see
+ * gpweno_set_halo): the side is a cut between the subdomains of one grid that
+ * is split into slabs along its slowest dimension, one slab per rank (the
+ * spatial domain decomposition of the paper's parallel runs, Section 6).
+ * Allowed on the slowest dimension only (x in 1D, y in 2D, z in 3D), which
+ * then needs at least R+3 cells. */
+typedef enum { GPWENO_BC_PERIODIC = 0, GPWENO_BC_OUTFLOW = 1, GPWENO_BC_EXTERNAL = 2 } gpweno_bc;
 
 typedef struct gpweno_plan_s *gpweno_plan;   /* opaque, owned by the library */
 
 /* Grid description.  ndim in {1,2,3}; n[d] cells and spacing dx[d] for
- * d < ndim (x, y, z order); bc_lo/bc_hi per dimension.  Periodic must be set
- * on both sides of a dimension or on neither. */
+ * d < ndim (x, y, z order); bc_lo/bc_hi per dimension (gpweno_bc).  Periodic
+ * must be set on both sides of a dimension or on neither. */
 typedef struct {
     int ndim;
     int n[3];
@@ -166,7 +173,8 @@ gpweno_status gpweno_gp_tables(int R, double ell_over_dx, double sigma_over_dx, 
  * they must not overlap. */
 gpweno_status gpweno_rhs(gpweno_plan plan, const void *U, void *dUdt, void *stream);
 
-/* One SSP-RK3 step in place on U (three fused stage launches):
+/* One SSP-RK3 step in place on U (three fused stage launches; plans with an
+ * external side step with gpweno_rk3_stage instead, GPWENO_ERR_ARG here):
  *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U <- 1/3 U + 2/3 (U2 + dt L(U2)),
  * carried in the equivalent increment form D1 = dt L(U), D2 = 1/4 (D1 + dt L(U+D1)),
  * U <- U + 2/3 (D2 + dt L(U+D2)), whose final sum is compensated (TwoSum): the
@@ -206,6 +214,62 @@ gpweno_status gpweno_rk3_step_noalloc(gpweno_plan plan, void *U, double dt, void
 
 /* *dt_dev (device double) = cfl / sum_d max over cells of (|u_d| + c)/dx_d. */
 gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *dt_dev, void *stream);
+
+/* ---- Slab decomposition of one grid over several ranks ---------------------
+ * One SSP-RK3 step of a slab whose plan has GPWENO_BC_EXTERNAL sides is three
+ * calls of gpweno_rk3_stage, and before each the G = R+3 boundary layers of
+ * that stage's input state are exchanged with the neighbouring slabs
+ * (Eq. disc_fd with the corrected flux of Eq. numFlux_cor reaches G cells):
+ *   for k in 0, 1, 2:
+ *       gpweno_halo_pack(plan, stage_input(k), send_lo, send_hi, stream);
+ *       send send_lo to the lower neighbour and send_hi to the upper one; receive
+ *       the lower neighbour's send_hi into recv_lo and the upper one's send_lo
+ *       into recv_hi (the caller's transport, e.g. NCCL send/recv);
+ *       gpweno_rk3_stage(plan, k, U, scratch, dt, dt_dev, stream);
+ * with stage_input(0) = U, stage_input(1) = scratch + 1 state, stage_input(2) =
+ * scratch + 2 states (the scratch layout of gpweno_rk3_step), and recv_lo /
+ * recv_hi registered once with gpweno_set_halo.  A CFL time step common to all
+ * ranks takes one max-reduction of three numbers per step (gpweno_rate_export,
+ * then gpweno_dt_from_rates).  Halo layout: [nc][G][layer], G layers of
+ * `layer` cells (nx*ny in 3D, nx in 2D, 1 in 1D) in increasing order of the
+ * slab coordinate: recv_lo holds the G cells just below the slab, recv_hi the G
+ * cells just above it. */
+
+/* Register the device halo buffers the kernels read for the plan's external
+ * sides (each nc*G*layer elements of the plan's dtype, 16-byte aligned, owned
+ * by the caller and alive while the plan steps); a side that is not external
+ * ignores its pointer (may be NULL).  GPWENO_ERR_ARG if an external side gets
+ * NULL or the plan has no external side. */
+gpweno_status gpweno_set_halo(gpweno_plan plan, const void *recv_lo, const void *recv_hi);
+
+/* Copy the first G and the last G layers of `state` (a device state of the
+ * plan's shape) along the slowest dimension into send_lo and send_hi (halo
+ * layout, either may be NULL).  One kernel launch on `stream`.  The slowest
+ * dimension must have at least G cells. */
+gpweno_status gpweno_halo_pack(gpweno_plan plan, const void *state, void *send_lo, void *send_hi, void *stream);
+
+/* Stage k (0, 1, 2) of gpweno_rk3_step on the same buffers (U, 4-state scratch,
+ * dt / dt_dev), one fused launch (two in 3D).  Stage 2 with dt_dev and a plan
+ * cfl > 0 accumulates the maxima of (|u_d|+c)/dx_d of the new state in the
+ * plan's rate buffer but does not compute the next dt (see gpweno_rate_export).
+ * External sides read the registered halo buffers, which must hold stage k's
+ * input layers of the neighbours when the launch runs. */
+gpweno_status gpweno_rk3_stage(gpweno_plan plan, int stage, void *U, void *scratch, double dt, void *dt_dev,
+                               void *stream);
+
+/* Accumulate the maxima of (|u_d|+c)/dx_d over the cells of U in the plan's
+ * rate buffer (for a common initial time step across ranks). */
+gpweno_status gpweno_rates(gpweno_plan plan, const void *U, void *stream);
+
+/* Copy the plan's three rate maxima (x, y, z; as the bit patterns of
+ * non-negative doubles, which order like the doubles, so an unsigned 64-bit
+ * max-reduction across ranks is the max of the rates) to the device buffer
+ * `rates` (3 x uint64) and clear the plan's buffer.  One launch. */
+gpweno_status gpweno_rate_export(gpweno_plan plan, void *rates, void *stream);
+
+/* *dt_dev = cfl / sum_d rates[d] with rates as written by gpweno_rate_export
+ * (typically after a max-reduction across ranks).  One launch. */
+gpweno_status gpweno_dt_from_rates(gpweno_plan plan, const void *rates, double cfl, void *dt_dev, void *stream);
 
 /* Host-only: the double-double GP-AO tables of a plan with ao = 1 (for
  * checking the precompute without a device).  w_hi: 2 x (2R+1) weights of the

@@ -1,5 +1,6 @@
 // C ABI of the GP-WENO library: plan lifetime, argument checks, the RK3 step
 // sequence and error reporting.  Kernels live in stage_f32.cu / stage_f64.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -151,8 +152,19 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
             set_error("dimension %d: periodic must be set on both sides or neither", d);
             return GPWENO_ERR_ARG;
         }
-        if ((dims->bc_lo[d] != 0 && dims->bc_lo[d] != 1) || (dims->bc_hi[d] != 0 && dims->bc_hi[d] != 1)) {
+        if (dims->bc_lo[d] < 0 || dims->bc_lo[d] > 2 || dims->bc_hi[d] < 0 || dims->bc_hi[d] > 2) {
             set_error("dimension %d: unknown boundary condition", d);
+            return GPWENO_ERR_ARG;
+        }
+        const bool ext = dims->bc_lo[d] == GPWENO_BC_EXTERNAL || dims->bc_hi[d] == GPWENO_BC_EXTERNAL;
+        if (ext && d != dims->ndim - 1) {
+            set_error("dimension %d: external (halo) sides are allowed on the slowest dimension %d only", d,
+                      dims->ndim - 1);
+            return GPWENO_ERR_ARG;
+        }
+        if (ext && dims->n[d] < R + 3) {
+            set_error("dimension %d: a slab with external sides needs at least R+3 = %d cells, has %d", d, R + 3,
+                      dims->n[d]);
             return GPWENO_ERR_ARG;
         }
         ncell *= dims->n[d];
@@ -288,41 +300,105 @@ static gpweno_status launch_stage(gpweno_plan p, const StageIO &io, cudaStream_t
 
 namespace gpweno {
 
-gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, void *lo, double dt,
-                           const double *dt_dev, bool want_rate, cudaStream_t st)
+// Buffers and weights of stage k of the increment-form SSP-RK3 step.  The 3D
+// x+y part of L goes through the buffer the stage update overwrites next: V1,
+// V2, then the dead V1.
+static StageIO stage_io(int k, void *U, void *D, void *V1, void *V2, void *lo, double dt, const double *dt_dev,
+                        bool want_rate)
 {
-    gpweno_status s;
     StageIO io;
     io.dt = dt;
     io.dt_dev = dt_dev;
-    // D_1 = dt L(U^n), V_1 = U^n + D_1   (3D: the x+y part of L goes through the
-    // buffer the stage update overwrites next: V1, V2, then the dead V1)
-    io.P = V1;
-    io.U = U;
     io.U0 = U;
-    io.Dout = D;
-    io.Vout = V1;
-    io.b = 1.0;
-    io.mode = 1;
-    if ((s = launch_stage(p, io, st)) != GPWENO_OK) return s;
-    // D_2 = 1/4 (D_1 + dt L(V_1)), V_2 = U^n + D_2
-    io.U = V1;
-    io.Din = D;
-    io.Vout = V2;
-    io.P = V2;
-    io.b = 0.25;
-    if ((s = launch_stage(p, io, st)) != GPWENO_OK) return s;
-    // U^{n+1} = U^n + 2/3 (D_2 + dt L(V_2)), compensated with lo
-    io.U = V2;
-    io.Dout = nullptr;
-    io.Vout = nullptr;
-    io.P = V1;
-    io.out = U;
-    io.lo = lo;
-    io.b = 2.0 / 3.0;
-    io.mode = 2;
-    io.want_rate = want_rate;
-    return launch_stage(p, io, st);
+    if (k == 0) {          // D_1 = dt L(U^n), V_1 = U^n + D_1
+        io.P = V1;
+        io.U = U;
+        io.Dout = D;
+        io.Vout = V1;
+        io.b = 1.0;
+        io.mode = 1;
+    } else if (k == 1) {   // D_2 = 1/4 (D_1 + dt L(V_1)), V_2 = U^n + D_2
+        io.P = V2;
+        io.U = V1;
+        io.Din = D;
+        io.Dout = D;
+        io.Vout = V2;
+        io.b = 0.25;
+        io.mode = 1;
+    } else {               // U^{n+1} = U^n + 2/3 (D_2 + dt L(V_2)), compensated with lo
+        io.P = V1;
+        io.U = V2;
+        io.Din = D;
+        io.out = U;
+        io.lo = lo;
+        io.b = 2.0 / 3.0;
+        io.mode = 2;
+        io.want_rate = want_rate;
+    }
+    return io;
+}
+
+gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, void *lo, double dt,
+                           const double *dt_dev, bool want_rate, cudaStream_t st)
+{
+    for (int k = 0; k < 3; ++k) {
+        gpweno_status s = launch_stage(p, stage_io(k, U, D, V1, V2, lo, dt, dt_dev, want_rate), st);
+        if (s != GPWENO_OK) return s;
+    }
+    return GPWENO_OK;
+}
+
+bool has_external_side(const gpweno_plan_s *p)
+{
+    const int sd = p->dims.ndim - 1;
+    return p->dims.bc_lo[sd] == GPWENO_BC_EXTERNAL || p->dims.bc_hi[sd] == GPWENO_BC_EXTERNAL;
+}
+
+// The halo buffers an external side needs are registered.
+static gpweno_status check_halo(const gpweno_plan_s *p, const char *what)
+{
+    const int sd = p->dims.ndim - 1;
+    if ((p->dims.bc_lo[sd] == GPWENO_BC_EXTERNAL && !p->halo[0]) ||
+        (p->dims.bc_hi[sd] == GPWENO_BC_EXTERNAL && !p->halo[1])) {
+        set_error("%s: the plan has external sides but no halo buffer was registered (gpweno_set_halo)", what);
+        return GPWENO_ERR_ARG;
+    }
+    return GPWENO_OK;
+}
+
+// Copy the first and last G layers of a state along the slab dimension into
+// the halo layout [nc][G][layer].
+template <typename T>
+__global__ void halo_pack_kernel(const T *__restrict__ s, T *lo, T *hi, long layer, int G, int n, int nc, long cstride)
+{
+    const long per_side = (long)nc * G * layer, block = (long)G * layer;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * per_side; i += (long)gridDim.x * blockDim.x) {
+        const int side = i >= per_side ? 1 : 0;
+        T *dst = side ? hi : lo;
+        if (!dst) continue;
+        const long j = i - side * per_side;
+        const long c = j / block, r = j - c * block;
+        dst[j] = s[c * cstride + (side ? (long)(n - G) * layer : 0L) + r];
+    }
+}
+
+// Copy the plan's rate maxima out and clear them.
+__global__ void rate_export_kernel(unsigned long long *ws, unsigned long long *out)
+{
+    if (threadIdx.x < 3) {
+        out[threadIdx.x] = ws[threadIdx.x];
+        ws[threadIdx.x] = 0ull;
+    }
+}
+
+// dt = cfl / sum_d rate_d from a caller's (reduced) rate maxima.
+__global__ void dt_from_rates_kernel(const unsigned long long *rate, int ndim, double cfl, double *dt_dev)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int d = 0; d < ndim; ++d) s += __longlong_as_double((long long)rate[d]);
+        *dt_dev = cfl / s;
+    }
 }
 
 }  // namespace gpweno
@@ -342,12 +418,127 @@ gpweno_status gpweno_rhs(gpweno_plan p, const void *U, void *dUdt, void *stream)
         set_error("gpweno_rhs: U and dUdt must be distinct 16-byte aligned buffers");
         return GPWENO_ERR_ARG;
     }
+    gpweno_status s = check_halo(p, "gpweno_rhs");
+    if (s != GPWENO_OK) return s;
     StageIO io;
     io.U = U;
     io.out = dUdt;
     io.P = dUdt;
     io.mode = 0;
     return launch_stage(p, io, (cudaStream_t)stream);
+}
+
+gpweno_status gpweno_set_halo(gpweno_plan p, const void *recv_lo, const void *recv_hi)
+{
+    if (!p || p->is_batch || !has_external_side(p)) {
+        set_error("gpweno_set_halo: needs a single-grid plan with an external side");
+        return GPWENO_ERR_ARG;
+    }
+    const int sd = p->dims.ndim - 1;
+    const bool elo = p->dims.bc_lo[sd] == GPWENO_BC_EXTERNAL, ehi = p->dims.bc_hi[sd] == GPWENO_BC_EXTERNAL;
+    if ((elo && (!recv_lo || !aligned16(recv_lo))) || (ehi && (!recv_hi || !aligned16(recv_hi)))) {
+        set_error("gpweno_set_halo: every external side needs a 16-byte aligned halo buffer");
+        return GPWENO_ERR_ARG;
+    }
+    p->halo[0] = elo ? recv_lo : nullptr;
+    p->halo[1] = ehi ? recv_hi : nullptr;
+    return GPWENO_OK;
+}
+
+gpweno_status gpweno_halo_pack(gpweno_plan p, const void *state, void *send_lo, void *send_hi, void *stream)
+{
+    g_launches = 0;
+    if (!p || p->is_batch || !state || !aligned16(state)) {
+        set_error("gpweno_halo_pack: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    const int sd = p->dims.ndim - 1, G = p->R + 3, n = p->dims.n[sd];
+    if (n < G) {
+        set_error("gpweno_halo_pack: the slowest dimension has %d cells, fewer than G = %d", n, G);
+        return GPWENO_ERR_ARG;
+    }
+    if (!send_lo && !send_hi) return GPWENO_OK;
+    const long layer = p->ncell / n;
+    const long total = 2L * (p->dims.ndim + 2) * G * layer;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 8L * p->num_sms);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->opts.dtype == GPWENO_F32)
+        halo_pack_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(state), static_cast<float *>(send_lo),
+                                                        static_cast<float *>(send_hi), layer, G, n, p->dims.ndim + 2,
+                                                        p->ncell);
+    else
+        halo_pack_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(state),
+                                                         static_cast<double *>(send_lo), static_cast<double *>(send_hi),
+                                                         layer, G, n, p->dims.ndim + 2, p->ncell);
+    GPW_CHECK(cudaGetLastError(), "halo pack kernel launch");
+    count_launch(1);
+    return GPWENO_OK;
+}
+
+gpweno_status gpweno_rk3_stage(gpweno_plan p, int stage, void *U, void *scratch, double dt, void *dt_dev,
+                               void *stream)
+{
+    g_launches = 0;
+    if (!p || p->is_batch || !U || !scratch || stage < 0 || stage > 2) {
+        set_error("gpweno_rk3_stage: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    if (!aligned16(U) || !aligned16(scratch)) {
+        set_error("gpweno_rk3_stage: buffers must be 16-byte aligned");
+        return GPWENO_ERR_ARG;
+    }
+    if (!dt_dev && !(dt > 0.0)) {
+        set_error("gpweno_rk3_stage: dt=%g must be positive", dt);
+        return GPWENO_ERR_ARG;
+    }
+    gpweno_status s = check_halo(p, "gpweno_rk3_stage");
+    if (s != GPWENO_OK) return s;
+    const size_t esz = p->opts.dtype == GPWENO_F32 ? 4 : 8;
+    const size_t bytes = esz * (size_t)(p->dims.ndim + 2) * (size_t)p->ncell;
+    char *base = static_cast<char *>(scratch);
+    const bool cfl = dt_dev && p->opts.cfl > 0.0;
+    return launch_stage(p,
+                        stage_io(stage, U, base, base + bytes, base + 2 * bytes, base + 3 * bytes, dt,
+                                 static_cast<const double *>(dt_dev), cfl),
+                        (cudaStream_t)stream);
+}
+
+gpweno_status gpweno_rates(gpweno_plan p, const void *U, void *stream)
+{
+    g_launches = 0;
+    if (!p || p->is_batch || !U) {
+        set_error("gpweno_rates: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->opts.dtype == GPWENO_F32 ? launch_max_rate_f32(p, U, st) : launch_max_rate_f64(p, U, st);
+}
+
+gpweno_status gpweno_rate_export(gpweno_plan p, void *rates, void *stream)
+{
+    g_launches = 0;
+    if (!p || !rates) {
+        set_error("gpweno_rate_export: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    rate_export_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(p->ws, static_cast<unsigned long long *>(rates));
+    GPW_CHECK(cudaGetLastError(), "rate export kernel launch");
+    count_launch(1);
+    return GPWENO_OK;
+}
+
+gpweno_status gpweno_dt_from_rates(gpweno_plan p, const void *rates, double cfl, void *dt_dev, void *stream)
+{
+    g_launches = 0;
+    if (!p || !rates || !dt_dev || !(cfl > 0.0)) {
+        set_error("gpweno_dt_from_rates: invalid argument");
+        return GPWENO_ERR_ARG;
+    }
+    dt_from_rates_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(static_cast<const unsigned long long *>(rates),
+                                                             p->dims.ndim, cfl, static_cast<double *>(dt_dev));
+    GPW_CHECK(cudaGetLastError(), "dt kernel launch");
+    count_launch(1);
+    return GPWENO_OK;
 }
 
 gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, void *dt_dev, void *stream)
@@ -363,6 +554,11 @@ gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, 
     }
     if (!dt_dev && !(dt > 0.0)) {
         set_error("gpweno_rk3_step: dt=%g must be positive", dt);
+        return GPWENO_ERR_ARG;
+    }
+    if (has_external_side(p)) {
+        set_error("gpweno_rk3_step: the plan has external sides; step it with gpweno_rk3_stage and a halo "
+                  "exchange before each stage");
         return GPWENO_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -423,6 +619,10 @@ gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int 
         gpweno_plan p = plans[k];
         if (!p || p->is_batch || p->dims.ndim != 2) {
             set_error("gpweno_plan_batch: plan %d is not a 2D single-grid plan", k);
+            return GPWENO_ERR_ARG;
+        }
+        if (has_external_side(p)) {
+            set_error("gpweno_plan_batch: plan %d has external (halo) sides, which batches do not support", k);
             return GPWENO_ERR_ARG;
         }
         if (p->opts.beta_mean || p->opts.scheme || p->opts.ao) {

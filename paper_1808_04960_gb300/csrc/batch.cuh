@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT)
             }
             a.cstride = (long)I.n[0] * I.n[1];
             a.P = nullptr;
+            a.slab_dim = -1;   // batch instances have no external sides
+            a.ext[0] = a.ext[1] = 0;
+            a.halo[0] = a.halo[1] = nullptr;
             sa = a;
             ssg = sg;
             sR = I.R;

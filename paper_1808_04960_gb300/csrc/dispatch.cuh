@@ -158,6 +158,12 @@ StageArgs<T> base_args(const gpweno_plan_s *p)
     a.flags = reinterpret_cast<int *>(p->ws + 3);
     a.cstride = p->ncell;
     a.P = nullptr;
+    const int sd = p->dims.ndim - 1;   // the slab dimension: the slowest one
+    a.ext[0] = p->dims.bc_lo[sd] == GPWENO_BC_EXTERNAL;
+    a.ext[1] = p->dims.bc_hi[sd] == GPWENO_BC_EXTERNAL;
+    a.slab_dim = (a.ext[0] || a.ext[1]) ? sd : -1;
+    a.halo[0] = static_cast<const T *>(p->halo[0]);
+    a.halo[1] = static_cast<const T *>(p->halo[1]);
     return a;
 }
 

@@ -112,6 +112,10 @@ extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double 
         set_error("gpweno_rk3_step_noalloc: U must be 16-byte aligned");
         return GPWENO_ERR_ARG;
     }
+    if (has_external_side(p)) {
+        set_error("gpweno_rk3_step_noalloc: plans with external sides step stage by stage (gpweno_rk3_stage)");
+        return GPWENO_ERR_ARG;
+    }
     if (!(dt > 0.0)) {
         set_error("gpweno_rk3_step_noalloc: dt=%g must be positive", dt);
         return GPWENO_ERR_ARG;

@@ -30,6 +30,7 @@ struct gpweno_plan_s {
     // device workspace: [0..2] rate maxima (double bits), [3] flags
     unsigned long long *ws = nullptr;
     gpweno::Schedule sched;
+    const void *halo[2] = {nullptr, nullptr};   // halo buffers of external sides (gpweno_set_halo)
     bool is_batch = false;
     // batch-only data
     std::vector<gpweno_plan> members;
@@ -76,6 +77,8 @@ struct StageIO {
 // D, V1, V2 are state-sized stage buffers; lo is the compensation remainder (or null).
 gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, void *lo, double dt,
                            const double *dt_dev, bool want_rate, cudaStream_t st);
+// Whether the plan has a GPWENO_BC_EXTERNAL side (slab decomposition).
+bool has_external_side(const gpweno_plan_s *p);
 
 // dispatch entry points implemented in stage_f32.cu / stage_f64.cu
 gpweno_status launch_stage_f32(gpweno_plan p, const StageIO &io, cudaStream_t st);

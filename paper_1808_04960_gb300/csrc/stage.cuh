@@ -59,7 +59,32 @@ struct StageArgs {
     unsigned long long *rate;  // if non-null: atomic max of (|u_d| + c)/dx_d of the result (double bits)
     int *flags;                // bit 0: non-physical state met
     int W, nstrips, H, nseg;   // schedule: strip width, #strips, segment height, #segments
+    // Slab decomposition: along the slowest dimension (slab_dim = ndim-1, or -1 if no side is
+    // external) the ghost layers of an external side come from a caller-filled halo buffer of
+    // G = R+3 layers, [nc][G][layer], layer k = the k-th cell beyond the side in increasing order.
+    int slab_dim;
+    int ext[2];                // low / high side external
+    const T *halo[2];          // halo buffers of the low / high side
 };
+
+// Source of layer g (a cell index along the slab dimension, possibly a ghost) of a
+// state whose layers are `unit` cells apart: the state itself, or an external halo.
+// `cs` receives the distance between components at that source.
+template <typename T>
+__device__ __forceinline__ const T *layer_src(const StageArgs<T> &a, const T *U, int g, int n, int per, long unit,
+                                              int G, long &cs)
+{
+    if (g < 0 && a.ext[0]) {
+        cs = (long)G * unit;
+        return a.halo[0] + (long)(g + G) * unit;
+    }
+    if (g >= n && a.ext[1]) {
+        cs = (long)G * unit;
+        return a.halo[1] + (long)(g - n) * unit;
+    }
+    cs = a.cstride;
+    return U + (long)bc_map(g, n, per) * unit;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -172,8 +197,18 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     const T idx[3] = {a.idx[0], a.idx[1], a.idx[2]};
 
     auto load_row = [&](int g) {
-        const int gy = bc_map(g, ny, a.per[1]);
         T *dst = ring + RG::slot(g) * (NC * STRIDE);
+        if (NC == 4 && a.slab_dim == 1 && ((g < 0 && a.ext[0]) || (g >= ny && a.ext[1]))) {
+            // a ghost row of an external side: from the halo buffer [nc][G][nx]
+            const T *src = g < 0 ? a.halo[0] + (long)(g + G) * nx : a.halo[1] + (long)(g - ny) * nx;
+            for (int col = tid; col < rowlen; col += NT) {
+                const int gx = bc_map(x0 - G + col, nx, a.per[0]);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * STRIDE + col, src + (long)c * G * nx + gx);
+            }
+            return;
+        }
+        const int gy = bc_map(g, ny, a.per[1]);
         const T *src = a.U + zoff + (long)gy * nx;
         for (int col = tid; col < rowlen; col += NT) {
             const int gx = bc_map(x0 - G + col, nx, a.per[0]);
@@ -504,11 +539,13 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
 
     auto load_plane = [&](int g) {
         if (!col_ok) return;
-        const int gz = bc_map(g, nz, a.per[2]);
+        constexpr int G = R + 3;
         T *dst = ring + RZ::slot(g) * (NC * NT) + tid;
-        const T *src = a.U + (long)gz * plane + col;
+        long ccs = cs;
+        const T *src = (a.slab_dim == 2 ? layer_src<T>(a, a.U, g, nz, a.per[2], plane, G, ccs)
+                                        : a.U + (long)bc_map(g, nz, a.per[2]) * plane) + col;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * NT, src + c * cs);
+        for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * NT, src + c * ccs);
     };
     for (int g = s_begin - R; g <= s_begin + 1 + R; ++g) load_plane(g);
     cp_async_commit();
@@ -642,9 +679,11 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
         const int x0 = item * a.W;
         const int Wc = min(a.W, nx - x0);
         for (int col = tid; col < Wc + 2 * G; col += NT) {
-            const int gx = bc_map(x0 - G + col, nx, a.per[0]);
+            long cs = nx;
+            const T *src = a.slab_dim == 0 ? layer_src<T>(a, a.U, x0 - G + col, nx, a.per[0], 1, G, cs)
+                                           : a.U + bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) row[c * STRIDE + col] = a.U[(long)c * nx + gx];
+            for (int c = 0; c < NC; ++c) row[c * STRIDE + col] = src[c * cs];
         }
         __syncthreads();
         if (tid < Wc + 5) {

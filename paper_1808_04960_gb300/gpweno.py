@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gpweno.h")
 
 OK, ERR_ARG, ERR_PRECOMPUTE, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT = range(6)
 F32, F64 = 0, 1
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, EXTERNAL = 0, 1, 2
 
 
 class GpwenoError(RuntimeError):
@@ -66,6 +66,12 @@ def load(path: str | None = None):
             "gpweno_ao_tables": (i, [i, d, d, dp, dp, dp, dp, dp, dp]),
             "gpweno_rhs": (i, [vp, vp, vp, vp]),
             "gpweno_rk3_step": (i, [vp, vp, vp, d, vp, vp]),
+            "gpweno_rk3_stage": (i, [vp, i, vp, vp, d, vp, vp]),
+            "gpweno_set_halo": (i, [vp, vp, vp]),
+            "gpweno_halo_pack": (i, [vp, vp, vp, vp, vp]),
+            "gpweno_rates": (i, [vp, vp, vp]),
+            "gpweno_rate_export": (i, [vp, vp, vp]),
+            "gpweno_dt_from_rates": (i, [vp, vp, d, vp, vp]),
             "gpweno_cfl_dt": (i, [vp, vp, d, vp, vp]),
             "gpweno_flags": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
             "gpweno_plan_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, ctypes.c_char_p]),
@@ -142,14 +148,16 @@ def _stream_handle(stream):
 def _bc_code(b):
     if isinstance(b, int):
         return b
-    return {"periodic": PERIODIC, "outflow": OUTFLOW}[b]
+    return {"periodic": PERIODIC, "outflow": OUTFLOW, "external": EXTERNAL}[b]
 
 
 class Plan:
     """A GP-WENO plan for one grid (see gpweno_plan_create).
 
     shape: interior grid in array order ((nx,), (ny, nx)); dx: spacing in
-    (x, y) order; bc: (lo, hi) pairs in (x, y) order, 'periodic' or 'outflow'.
+    (x, y) order; bc: (lo, hi) pairs in (x, y) order, 'periodic', 'outflow' or
+    'external' (a slab side whose ghost layers come from a halo buffer; slowest
+    dimension only, see set_halo and rk3_stage).
     """
 
     def __init__(self, R, ell_over_dx, shape, dx, bc, gamma=1.4, sigma_over_dx=3.0, eps=1e-36, p=2,
@@ -268,6 +276,89 @@ class Plan:
         _check(fn(self.handle, ctypes.c_void_p(U.data_ptr()), float(dt), _stream_handle(stream)),
                "gpweno_rk3_step_noalloc")
         return U
+
+    # ---- slab decomposition (gpweno_set_halo, gpweno_halo_pack, gpweno_rk3_stage, ...) ----
+
+    @property
+    def ghost(self) -> int:
+        """G = R+3 ghost layers per side."""
+        return self.R + 3
+
+    def halo_shape(self):
+        """Shape of one side's halo buffer: (nc, G) + the shape of one layer of the slowest axis."""
+        return (self.nc, self.ghost) + self.shape[1:]
+
+    def new_halo(self):
+        import torch
+        return torch.zeros(self.halo_shape(), dtype=self.dtype, device="cuda")
+
+    def _check_halo(self, h, name):
+        import torch
+        if h is None:
+            return None
+        if (not isinstance(h, torch.Tensor) or not h.is_cuda or h.dtype != self.dtype
+                or tuple(h.shape) != self.halo_shape() or not h.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of shape {self.halo_shape()} and the plan's dtype")
+        return ctypes.c_void_p(h.data_ptr())
+
+    def set_halo(self, recv_lo, recv_hi):
+        """Register the halo buffers the kernels read for the external sides (kept referenced here)."""
+        lo, hi = self._check_halo(recv_lo, "recv_lo"), self._check_halo(recv_hi, "recv_hi")
+        _check(self.lib.gpweno_set_halo(self.handle, lo, hi), "gpweno_set_halo")
+        self._halo = (recv_lo, recv_hi)
+
+    def halo_pack(self, state, send_lo, send_hi, stream=None):
+        """The first and last G layers of `state` along the slowest axis into send_lo / send_hi."""
+        self._check_state(state, "state")
+        _check(self.lib.gpweno_halo_pack(self.handle, ctypes.c_void_p(state.data_ptr()),
+                                         self._check_halo(send_lo, "send_lo"), self._check_halo(send_hi, "send_hi"),
+                                         _stream_handle(stream)), "gpweno_halo_pack")
+
+    @staticmethod
+    def stage_input(k, U, scratch):
+        """The stencil state stage k reads (the state whose halo layers are exchanged before it)."""
+        return U if k == 0 else scratch[k]
+
+    def rk3_stage(self, k, U, scratch, dt=0.0, dt_dev=None, stream=None):
+        """Stage k (0, 1, 2) of rk3_step on the same buffers."""
+        import torch
+        self._check_state(U)
+        if (scratch.dtype != self.dtype or tuple(scratch.shape) != (4, self.nc) + self.shape
+                or not scratch.is_contiguous() or not scratch.is_cuda):
+            raise ValueError("scratch must be a contiguous CUDA tensor of shape (4, nc, ...) and the plan's dtype")
+        dptr = None
+        if dt_dev is not None:
+            if dt_dev.dtype != torch.float64 or not dt_dev.is_cuda or dt_dev.numel() != 1:
+                raise ValueError("dt_dev must be a CUDA float64 tensor with one element")
+            dptr = ctypes.c_void_p(dt_dev.data_ptr())
+        _check(self.lib.gpweno_rk3_stage(self.handle, int(k), ctypes.c_void_p(U.data_ptr()),
+                                         ctypes.c_void_p(scratch.data_ptr()), float(dt), dptr,
+                                         _stream_handle(stream)), "gpweno_rk3_stage")
+
+    def rates(self, U, stream=None):
+        """Accumulate the maxima of (|u_d|+c)/dx_d of U in the plan's rate buffer."""
+        self._check_state(U)
+        _check(self.lib.gpweno_rates(self.handle, ctypes.c_void_p(U.data_ptr()), _stream_handle(stream)),
+               "gpweno_rates")
+
+    def rate_export(self, rates, stream=None):
+        """Move the plan's three rate maxima (double bit patterns) into `rates` (CUDA int64, 3)."""
+        import torch
+        if rates.dtype != torch.int64 or not rates.is_cuda or rates.numel() != 3 or not rates.is_contiguous():
+            raise ValueError("rates must be a contiguous CUDA int64 tensor with 3 elements")
+        _check(self.lib.gpweno_rate_export(self.handle, ctypes.c_void_p(rates.data_ptr()), _stream_handle(stream)),
+               "gpweno_rate_export")
+
+    def dt_from_rates(self, rates, cfl, dt_dev, stream=None):
+        """dt_dev = cfl / sum_d rates[d] (rates as exported, e.g. after a max-reduction over ranks)."""
+        import torch
+        if rates.dtype != torch.int64 or not rates.is_cuda or rates.numel() != 3:
+            raise ValueError("rates must be a CUDA int64 tensor with 3 elements")
+        if dt_dev.dtype != torch.float64 or not dt_dev.is_cuda or dt_dev.numel() != 1:
+            raise ValueError("dt_dev must be a CUDA float64 tensor with one element")
+        _check(self.lib.gpweno_dt_from_rates(self.handle, ctypes.c_void_p(rates.data_ptr()), float(cfl),
+                                             ctypes.c_void_p(dt_dev.data_ptr()), _stream_handle(stream)),
+               "gpweno_dt_from_rates")
 
     def cfl_dt(self, U, cfl, dt_dev, stream=None):
         import torch
