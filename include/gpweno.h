@@ -54,7 +54,8 @@ typedef enum { GPWENO_F32 = 0, GPWENO_F64 = 1 } gpweno_dtype;
  * layers of that side are supplied by the caller in a halo buffer (see
  * gpweno_set_halo): the side is a cut between the subdomains of one grid that
  * is split into slabs along its slowest dimension, one slab per rank (the
- * spatial domain decomposition of the paper's parallel runs, Section 6).
+ * paper's solver is parallelized over cores, Section 5, and its vortex timings
+ * of Section 6.2 ran on four).
  * Allowed on the slowest dimension only (x in 1D, y in 2D, z in 3D), which
  * then needs at least R+3 cells. */
 typedef enum { GPWENO_BC_PERIODIC = 0, GPWENO_BC_OUTFLOW = 1, GPWENO_BC_EXTERNAL = 2 } gpweno_bc;
@@ -243,9 +244,10 @@ gpweno_status gpweno_cfl_dt(gpweno_plan plan, const void *U, double cfl, void *d
 gpweno_status gpweno_set_halo(gpweno_plan plan, const void *recv_lo, const void *recv_hi);
 
 /* Copy the first G and the last G layers of `state` (a device state of the
- * plan's shape) along the slowest dimension into send_lo and send_hi (halo
- * layout, either may be NULL).  One kernel launch on `stream`.  The slowest
- * dimension must have at least G cells. */
+ * plan's shape; it may be a stage buffer inside the scratch, so only element
+ * alignment is required) along the slowest dimension into send_lo and send_hi
+ * (halo layout, either may be NULL).  One kernel launch on `stream`.  The
+ * slowest dimension must have at least G cells. */
 gpweno_status gpweno_halo_pack(gpweno_plan plan, const void *state, void *send_lo, void *send_hi, void *stream);
 
 /* Stage k (0, 1, 2) of gpweno_rk3_step on the same buffers (U, 4-state scratch,
@@ -297,8 +299,11 @@ gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
  * which must outlive it.  tune_cache: NULL, or the path of a text file of
  * lines "<signature hex> <block 128|256> <ctas per SM>" (written by
  * paper_1808_04960_gb300/autotune.py); a line whose signature matches this
- * batch overrides the built-in block-size choice.  Allocates its schedule and
- * descriptor arrays on the device. */
+ * batch overrides the built-in block-size choice; a line may add three more
+ * fields "<strip width cap (0 = as the block allows)> <fewest rows of a segment
+ * that does not end its strip> <CTA shares per resident slot (1..4)>" (the
+ * tile shapes the autotuner searches).  Allocates its schedule and descriptor
+ * arrays on the device. */
 gpweno_status gpweno_plan_batch(gpweno_plan *out_batch, const gpweno_plan *plans, int n, const char *tune_cache);
 
 /* One SSP-RK3 step of every instance of a batch plan, in place:
@@ -316,6 +321,11 @@ gpweno_status gpweno_batch_rk3_step(gpweno_plan batch, void *const *U, void *con
  * assumed, CTAs per launch, number of segments, instance-list signature. */
 int gpweno_batch_info(gpweno_plan batch, int *block, int *ctas_per_sm, int *grid, int *segments,
                       unsigned long long *signature);
+
+/* Tile shapes of a batch plan's schedule: the widest strip (columns), the
+ * fewest rows of a segment that does not finish its strip, and CTA shares per
+ * resident CTA slot. */
+int gpweno_batch_tiles(gpweno_plan batch, int *strip_width_cap, int *min_rows, int *ctas_per_slot);
 
 /* Number of kernel launches the last step function issued (for launch accounting). */
 int gpweno_last_launch_count(void);

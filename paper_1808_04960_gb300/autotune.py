@@ -1,20 +1,31 @@
-"""Measured autotuning of the batched stage kernel's schedule.
+"""Measured autotuning of the batched stage kernel's schedule and tile shapes.
 
 For one batch (a list of plans with their state and scratch tensors) every
-candidate (block size, CTAs per SM) is forced through the library's tuning
-cache, a batch plan is built with it, and a few SSP-RK3 steps are timed with
-CUDA events on clones of the states.  The fastest candidate is written to the
-cache file as "<signature hex> <block> <ctas per SM>", which
-gpweno_plan_batch reads for batches with the same instance list.
+candidate schedule -- block size, resident CTAs per SM, the cap on a strip's
+width, the fewest rows of a segment that does not end its strip, and CTA
+shares per resident slot -- is forced through the library's tuning cache, a
+batch plan is built with it, and a few SSP-RK3 steps are timed with CUDA
+events on clones of the states.  The fastest candidate is written to the cache
+file as "<signature hex> <block> <ctas per SM> <width cap> <min rows>
+<shares per slot>", which gpweno_plan_batch reads for batches with the same
+instance list.  Every candidate computes the same faces, so the results do not
+depend on the choice (the tests check this bitwise).
 """
 from __future__ import annotations
 
+import itertools
 import os
 import tempfile
 
 from . import gpweno
 
-CANDIDATES = ((128, 1), (128, 2), (128, 3), (128, 4), (256, 1), (256, 2))
+# (block, CTAs per SM) pairs the register budget allows, then the tile shapes
+BLOCKS = ((128, 2), (128, 3), (128, 4), (256, 1), (256, 2))
+WIDTH_CAPS = (0, 64, 96)         # 0: the widest strip the block allows (block - 5 columns)
+MIN_ROWS = (8, 24)
+SHARES_PER_SLOT = (1, 2)
+CANDIDATES = tuple((b, c, w, r, o) for (b, c), w, r, o in itertools.product(BLOCKS, WIDTH_CAPS, MIN_ROWS,
+                                                                            SHARES_PER_SLOT))
 
 
 def _time_batch(plans, Us, Ss, dt_dev, cache, steps, warmup):
@@ -38,22 +49,24 @@ def _time_batch(plans, Us, Ss, dt_dev, cache, steps, warmup):
 
 
 def tune_batch(plans, Us, Ss, dt_dev, cache_path=None, candidates=CANDIDATES, steps=3, warmup=1):
-    """Time every candidate schedule; return (best (block, ctas), {candidate: ms/step}).
+    """Time every candidate schedule; return (best candidate, {candidate: ms/step}), a candidate
+    being (block, CTAs per SM, width cap, min rows, shares per slot).
     If cache_path is given, the best line replaces any earlier line for this batch."""
     sig = gpweno.BatchPlan(plans).info()["signature"]
     timings = {}
     fd, tmp = tempfile.mkstemp(suffix=".txt")
     os.close(fd)
     try:
-        for block, cps in candidates:
+        for cand in candidates:
+            block, cps = cand[0], cand[1]
             with open(tmp, "w") as f:
-                f.write(f"{sig} {block} {cps}\n")
+                f.write(f"{sig} " + " ".join(str(x) for x in cand) + "\n")
             try:
                 ms, info = _time_batch(plans, Us, Ss, dt_dev, tmp, steps, warmup)
             except gpweno.GpwenoError:
                 continue
             if info["block"] == block and info["ctas_per_sm"] == cps:
-                timings[(block, cps)] = ms
+                timings[cand] = ms
     finally:
         os.unlink(tmp)
     best = min(timings, key=timings.get)
@@ -62,7 +75,7 @@ def tune_batch(plans, Us, Ss, dt_dev, cache_path=None, candidates=CANDIDATES, st
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 lines = [ln for ln in f if not ln.startswith(sig)]
-        lines.append(f"{sig} {best[0]} {best[1]}\n")
+        lines.append(f"{sig} " + " ".join(str(x) for x in best) + "\n")
         with open(cache_path, "w") as f:
             f.writelines(lines)
     return best, timings
@@ -93,8 +106,8 @@ def _main():
         Ss.append(p.new_scratch())
         dts.append(d)
     best, timings = tune_batch(plans, Us, Ss, torch.cat(dts), args.cache, steps=args.steps, warmup=2)
-    for (block, cps), ms in sorted(timings.items()):
-        print(f"block {block:4d}  ctas/SM {cps}  {ms:8.3f} ms/step")
+    for cand, ms in sorted(timings.items(), key=lambda kv: kv[1]):
+        print("block %4d  ctas/SM %d  width cap %3d  min rows %2d  shares/slot %d  %8.3f ms/step" % (cand + (ms,)))
     print("best", best, "->", args.cache)
 
 

@@ -448,8 +448,10 @@ gpweno_status gpweno_set_halo(gpweno_plan p, const void *recv_lo, const void *re
 gpweno_status gpweno_halo_pack(gpweno_plan p, const void *state, void *send_lo, void *send_hi, void *stream)
 {
     g_launches = 0;
-    if (!p || p->is_batch || !state || !aligned16(state)) {
-        set_error("gpweno_halo_pack: invalid argument");
+    const uintptr_t esz = p && p->opts.dtype == GPWENO_F32 ? 4 : 8;
+    if (!p || p->is_batch || !state || (reinterpret_cast<uintptr_t>(state) % esz) != 0 ||
+        (reinterpret_cast<uintptr_t>(send_lo) % esz) != 0 || (reinterpret_cast<uintptr_t>(send_hi) % esz) != 0) {
+        set_error("gpweno_halo_pack: invalid argument (null plan or state, or a buffer not aligned to its element)");
         return GPWENO_ERR_ARG;
     }
     const int sd = p->dims.ndim - 1, G = p->R + 3, n = p->dims.n[sd];
@@ -682,6 +684,15 @@ gpweno_status gpweno_batch_rk3_step(gpweno_plan b, void *const *U, void *const *
                                                       : launch_batch_stage_f64(b, stage, U, scratch, dt, st);
         if (s != GPWENO_OK) return s;
     }
+    return GPWENO_OK;
+}
+
+int gpweno_batch_tiles(gpweno_plan b, int *strip_width_cap, int *min_rows, int *ctas_per_slot)
+{
+    if (!b || !b->is_batch) return GPWENO_ERR_ARG;
+    if (strip_width_cap) *strip_width_cap = b->batch_wcap;
+    if (min_rows) *min_rows = b->batch_min_rows;
+    if (ctas_per_slot) *ctas_per_slot = b->batch_oversub;
     return GPWENO_OK;
 }
 

@@ -25,7 +25,7 @@ struct BatchInstInfo {
 // at most `grid` CTA shares of roughly equal estimated cost.  Returns the
 // number of CTAs used; fills segments and per-CTA start offsets.
 inline int partition_batch(const std::vector<BatchInstInfo> &info, const std::vector<int> &order, int grid,
-                           double budget, std::vector<BatchSeg> &segs, std::vector<int> &start)
+                           double budget, std::vector<BatchSeg> &segs, std::vector<int> &start, int min_rows = 8)
 {
     segs.clear();
     start.assign(1, 0);
@@ -38,7 +38,7 @@ inline int partition_batch(const std::vector<BatchInstInfo> &info, const std::ve
                 // rows affordable in this CTA after paying the segment warm-up
                 double avail = left - I.warm_cost;
                 int rows = avail > 0 ? (int)std::floor(avail / I.row_cost) : 0;
-                if (rows < 1 || (rows < 8 && I.ny - y > rows)) {
+                if (rows < 1 || (rows < min_rows && I.ny - y > rows)) {
                     if (left < budget) {       // close this CTA and open a fresh one
                         start.push_back((int)segs.size());
                         left = budget;
@@ -72,8 +72,16 @@ inline unsigned long long batch_hash(const std::vector<BatchInstInfo> &info)
     return h;
 }
 
-// Tuning cache: text lines "<signature hex> <block> <ctas_per_sm>".
-inline bool read_tune_cache(const char *path, unsigned long long sig, int &nt, int &cps)
+// Schedule parameters of a batch: block size, resident CTAs per SM, the cap on a
+// strip's width (columns), the fewest rows a segment may have when it does not
+// finish its strip, and CTA shares per resident slot.
+struct BatchTiles {
+    int nt = 0, cps = 0, wcap = 0, min_rows = 8, oversub = 1;
+};
+
+// Tuning cache: text lines "<signature hex> <block> <ctas_per_sm> [<strip width cap>
+// <min segment rows> <CTA shares per slot>]" (0 for the width cap: the block allows).
+inline bool read_tune_cache(const char *path, unsigned long long sig, BatchTiles &t)
 {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
@@ -82,11 +90,15 @@ inline bool read_tune_cache(const char *path, unsigned long long sig, int &nt, i
     bool found = false;
     while (std::fgets(line, sizeof(line), f)) {
         unsigned long long s;
-        int a, b;
-        if (std::sscanf(line, "%llx %d %d", &s, &a, &b) == 3 && s == sig && (a == 128 || a == 256) && b >= 1 &&
-            b <= 8) {
-            nt = a;
-            cps = b;
+        int a, b, w = 0, r = 8, o = 1;
+        const int got = std::sscanf(line, "%llx %d %d %d %d %d", &s, &a, &b, &w, &r, &o);
+        if ((got == 3 || got == 6) && s == sig && (a == 128 || a == 256) && b >= 1 && b <= 8 && w >= 0 &&
+            (w == 0 || w >= 16) && r >= 1 && r <= 1024 && o >= 1 && o <= 4) {
+            t.nt = a;
+            t.cps = b;
+            t.wcap = w;
+            t.min_rows = r;
+            t.oversub = o;
             found = true;
         }
     }
@@ -154,23 +166,28 @@ gpweno_status build_batch_T(gpweno_plan b)
         I.R = p->R;
     }
     b->batch_signature = batch_hash(info);
-    int nt = 0, cps = 0;
-    if (!read_tune_cache(b->batch_tune_path.empty() ? nullptr : b->batch_tune_path.c_str(), b->batch_signature, nt,
-                         cps)) {
+    BatchTiles tiles;
+    if (!read_tune_cache(b->batch_tune_path.empty() ? nullptr : b->batch_tune_path.c_str(), b->batch_signature,
+                         tiles)) {
         // built-in choice: narrow instances waste most lanes of a 256-thread strip
         std::vector<int> widths;
         for (const auto &I : info) widths.push_back(I.nx);
         std::nth_element(widths.begin(), widths.begin() + n / 2, widths.end());
-        nt = widths[n / 2] < 400 ? 128 : 256;
-        cps = 0;   // occupancy limit
+        tiles.nt = widths[n / 2] < 400 ? 128 : 256;
+        tiles.cps = 0;   // occupancy limit
     }
+    const int nt = tiles.nt;
+    int cps = tiles.cps;
     int occ = 0;
     gpweno_status s = nt == 128 ? batch_occupancy<T, 128>(occ) : batch_occupancy<T, 256>(occ);
     if (s != GPWENO_OK) return s;
     if (cps <= 0 || cps > occ) cps = occ;
     b->batch_nt = nt;
     b->batch_ctas_per_sm = cps;
-    const int wmax = nt - 5;
+    const int wmax = tiles.wcap > 0 ? std::min(nt - 5, tiles.wcap) : nt - 5;
+    b->batch_wcap = wmax;
+    b->batch_min_rows = tiles.min_rows;
+    b->batch_oversub = tiles.oversub;
     double total = 0.0;
     for (auto &I : info) {
         I.nstrips = (I.nx + wmax - 1) / wmax;
@@ -183,14 +200,14 @@ gpweno_status build_batch_T(gpweno_plan b)
     std::vector<int> order(n);
     for (int k = 0; k < n; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return info[x].R > info[y].R; });
-    const int grid = cps * b->num_sms;
+    const int grid = cps * b->num_sms * tiles.oversub;
     std::vector<BatchSeg> segs;
     std::vector<int> start;
     double budget = total / grid;
-    int used = partition_batch(info, order, grid, budget, segs, start);
+    int used = partition_batch(info, order, grid, budget, segs, start, tiles.min_rows);
     for (int it = 0; it < 60 && used > grid; ++it) {
         budget *= 1.01;
-        used = partition_batch(info, order, grid, budget, segs, start);
+        used = partition_batch(info, order, grid, budget, segs, start, tiles.min_rows);
     }
     b->batch_grid = used;
     b->batch_nseg = (int)segs.size();

@@ -36,6 +36,9 @@ struct gpweno_plan_s {
     std::vector<gpweno_plan> members;
     int batch_nt = 256;                     // block size of the batch kernel
     int batch_ctas_per_sm = 2;              // resident CTAs per SM the schedule assumes
+    int batch_wcap = 0;                     // widest strip (columns)
+    int batch_min_rows = 8;                 // fewest rows of a segment that does not end its strip
+    int batch_oversub = 1;                  // CTA shares per resident slot
     int batch_grid = 0;                     // CTAs per launch
     int batch_nseg = 0;                     // segments in the schedule
     unsigned long long batch_signature = 0; // hash of the instance list (tuning-cache key)

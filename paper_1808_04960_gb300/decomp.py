@@ -4,10 +4,10 @@ Slabs.  One grid is cut along its slowest axis (x in 1D, y in 2D, z in 3D) into
 one slab per rank; neighbouring slabs exchange G = R+3 boundary layers before
 every RK stage (the corrected flux of Eq. numFlux_cor differenced by Eq.
 disc_fd reaches G cells), and a common CFL time step takes one max-reduction
-of the three per-direction wavespeed maxima per step.  This is the domain
-decomposition of the paper's parallel runs (Section 6, the timing paragraph);
-here each slab is one GPU and the transport is torch.distributed (NCCL on
-GPUs, gloo on CPU tensors).  The cut sides of a slab are GPWENO_BC_EXTERNAL
+of the three per-direction wavespeed maxima per step.  The paper's solver is
+parallelized the same way across CPU cores (Section 5; its vortex timings of
+Section 6.2 ran on four cores); here each slab is one GPU and the transport is
+torch.distributed (NCCL on GPUs, gloo on CPU tensors).  The cut sides of a slab are GPWENO_BC_EXTERNAL
 sides of its plan; the outer sides keep the grid's boundary condition
 (periodic grids close the ring of slabs).
 

@@ -79,6 +79,7 @@ def load(path: str | None = None):
             "gpweno_last_launch_count": (i, []),
             "gpweno_batch_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i), ctypes.POINTER(ctypes.c_ulonglong)]),
+            "gpweno_batch_tiles": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "gpweno_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sigs.items():
@@ -404,8 +405,11 @@ class BatchPlan:
         sig = ctypes.c_ulonglong()
         _check(self.lib.gpweno_batch_info(self.handle, *[ctypes.byref(x) for x in v], ctypes.byref(sig)),
                "gpweno_batch_info")
+        t = [ctypes.c_int() for _ in range(3)]
+        _check(self.lib.gpweno_batch_tiles(self.handle, *[ctypes.byref(x) for x in t]), "gpweno_batch_tiles")
         return dict(block=v[0].value, ctas_per_sm=v[1].value, grid=v[2].value, segments=v[3].value,
-                    signature=f"{sig.value:016x}")
+                    signature=f"{sig.value:016x}", strip_width_cap=t[0].value, min_rows=t[1].value,
+                    ctas_per_slot=t[2].value)
 
     def flags(self) -> int:
         v = ctypes.c_int(0)

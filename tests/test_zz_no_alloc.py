@@ -47,7 +47,9 @@ def test_noalloc_matches_scratch_step(dtype, shape, tol, R):
     Ua = torch.from_numpy(U0).to("cuda", tdt).contiguous()
     Ub = Ua.clone()
     scratch = torch.zeros((4,) + tuple(Ua.shape), dtype=tdt, device="cuda")
-    dt = 0.2 * min(meta["dx"])
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.cfl_dt(Ua, 0.4, dt_dev)                     # CFL 0.4 of the initial state
+    dt = float(dt_dev.item())
     for call in range(2):
         plan.rk3_step(Ua, scratch, dt=dt)
         plan.rk3_step_noalloc(Ub, dt)
