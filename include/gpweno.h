@@ -111,7 +111,9 @@ typedef struct {
  *                  the GP-CWENO combination of the three 3-point stencils
  *                  (Eqs. cweno_stencil, nonlin-AO, CWENO-lin, GP-AO,
  *                  recursive-weights, AO-recursive), beta of each stencil the
- *                  data-fit term (1/2) f^T K_N(sigma)^-1 f of Eq. log-like.
+ *                  data-fit term (1/2) f^T K_N(sigma)^-1 f of Eq. log-like
+ *                  divided by its value on constant data, 1^T K_N^-1 1, so that
+ *                  stencils of different size N agree on smooth data.
  *                  Requires scheme = 0 and candidates = 0.
  *   ao_gamma_hi, ao_gamma_lo
  *                  gamma_HI and gamma_LO of Eq. CWENO-lin, in (0,1)

@@ -26,8 +26,9 @@ Parity status per function (pins are in ``tests/test_oracle_*.py``):
                             Eq. flux_2nd)
   GP-AO (gp_ao)             pinned (equal weights give the high-order GP
                             prediction; coefficients sum to one; smooth small
-                            stencils win at a jump; scheme invariants; measured
-                            smooth order ~3.4, below the paper's 2R+1 claim)
+                            stencils win at a jump; scheme invariants; smooth order
+                            above 4.3 with the size-normalised indicators, 3.4
+                            with the bare data-fit term)
 """
 from __future__ import annotations
 
@@ -79,7 +80,8 @@ class _Cfg(ctypes.Structure):
                 ("gr", ctypes.c_void_p), ("Kinv", ctypes.c_void_p), ("flux", ctypes.c_int),
                 ("beta_mean", ctypes.c_int), ("scheme", ctypes.c_int), ("ao", ctypes.c_int),
                 ("ao_gamma_hi", ctypes.c_double), ("ao_gamma_lo", ctypes.c_double), ("ao_l", ctypes.c_void_p),
-                ("ao_r", ctypes.c_void_p), ("ao_kinv", ctypes.c_void_p), ("ao_const", ctypes.c_double * 3)]
+                ("ao_r", ctypes.c_void_p), ("ao_kinv", ctypes.c_void_p), ("ao_const", ctypes.c_double * 3),
+                ("ao_scale", ctypes.c_double * 3)]
 
 
 def _load():
@@ -175,14 +177,16 @@ class Oracle:
 
     def __init__(self, shape, dx, bc, R=2, ell_over_dx=12.0, sigma_over_dx=3.0,
                  gamma=1.4, eps=1e-36, p=2, flux="lf", beta_mean=False, candidates="gp", scheme="fdprim",
-                 recon_weights=None, ao=False, ao_gamma_hi=0.85, ao_gamma_lo=0.85, ao_beta="datafit"):
+                 recon_weights=None, ao=False, ao_gamma_hi=0.85, ao_gamma_lo=0.85, ao_beta="normalized"):
         """scheme "fdprim": GP-WENO Riemann states, face flux, high-order correction (Section 2,
         Del Zanna's form); "fdflux": reconstruction of the split point fluxes (Section 2,
         Shu-Osher's form) with reconstruction weights unless recon_weights=False (the naive
         point-value weights of Eq. flux_2nd, kept for the order test).
         ao: GP-AO of Appendix A instead of GP-WENO (R = 2: AO(2,3); R = 3: AO(3,2,3)), with
-        beta the data-fit term of Eq. log-like ("datafit") or the whole negative log-likelihood
-        with Sigma = 1 ("loglik")."""
+        beta of each stencil the data-fit term of Eq. log-like divided by that of constant data,
+        (1/2) f^T K_N^-1 f / (1^T K_N^-1 1) ("normalized", the default: stencils of different
+        size then agree on smooth data), the data-fit term alone ("datafit"), or the whole
+        negative log-likelihood with Sigma = 1 ("loglik")."""
         self.lib = _load()
         shape = tuple(int(s) for s in shape)
         self.ndim = len(shape)
@@ -225,8 +229,12 @@ class Oracle:
             c.ao_l, c.ao_r, c.ao_kinv = [a.ctypes.data for a in self._keep[-3:]]
             c.ao_gamma_hi, c.ao_gamma_lo = float(ao_gamma_hi), float(ao_gamma_lo)
             for i, (k, n) in enumerate((("hi", 2 * R + 1), ("lo", 2 * R - 1), ("3", 3))):
+                c.ao_scale[i] = 1.0
                 if ao_beta == "loglik" and ("logdet_" + k) in tl:
                     c.ao_const[i] = 0.5 * n * math.log(2 * math.pi) + 0.5 * tl["logdet_" + k]
+                if ao_beta == "normalized" and ("one_" + k) in tl:
+                    # the data-fit term per unit of that of constant data, 1^T K_N^-1 1
+                    c.ao_scale[i] = 1.0 / tl["one_" + k]
         self.cfg = c
         self.R = int(R)
         self.gamma = float(gamma)

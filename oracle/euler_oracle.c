@@ -92,6 +92,7 @@ typedef struct {
     const double *ao_r;   /* the same at x* = -1/2 */
     const double *ao_kinv;/* K^-1 built with sigma: hi [(2R+1)^2], lo [(2R-1)^2] (R = 3 only), 3-point [9] */
     double ao_const[3];   /* constant terms added to beta of the hi, lo and 3-point stencils */
+    double ao_scale[3];   /* factors of the data-fit terms of the hi, lo and 3-point stencils */
 } oracle_cfg;
 
 static long ncells(const oracle_cfg *c) { return (long)c->n[0] * c->n[1] * c->n[2]; }
@@ -297,12 +298,13 @@ static double gp_weno(const oracle_cfg *c, const double *f, const double *w, con
 /* beta of one stencil for GP-AO: the data-fit term of the negative log-likelihood,
  * (1/2) f^T K^-1 f (Eq. log-like; f relative to the centre value with beta_mean),
  * plus the configured constant (the normalisation and complexity terms). */
-static double ao_beta(const oracle_cfg *c, const double *Kinv, const double *f, int n, double mean, double cst)
+static double ao_beta(const oracle_cfg *c, const double *Kinv, const double *f, int n, double mean, double cst,
+                      double scale)
 {
     double b = 0.0;
     for (int a = 0; a < n; ++a)
         for (int d = 0; d < n; ++d) b += (f[a] - mean) * Kinv[a * n + d] * (f[d] - mean);
-    return 0.5 * b + cst;
+    return scale * 0.5 * b + cst;
 }
 
 /* GP-AO(R,3) (Eq. GP-AO): the high-order prediction qh with its beta bh hybridised with the
@@ -337,16 +339,16 @@ static double gp_ao(const oracle_cfg *c, const double *f, const double *tab)
         const double *fm = f + R - 2 + m;     /* Eq. cweno_stencil: cells i-2..i, i-1..i+1, i..i+2 */
         q3[m] = 0.0;
         for (int j = 0; j < 3; ++j) q3[m] += w3[m * 3 + j] * fm[j];
-        b3[m] = ao_beta(c, K3, fm, 3, mean, c->ao_const[2]);
+        b3[m] = ao_beta(c, K3, fm, 3, mean, c->ao_const[2], c->ao_scale[2]);
     }
     double qh = 0.0;
     for (int j = 0; j < nh; ++j) qh += w_hi[j] * f[j];
-    double bh = ao_beta(c, K_hi, f, nh, mean, c->ao_const[0]);
+    double bh = ao_beta(c, K_hi, f, nh, mean, c->ao_const[0], c->ao_scale[0]);
     double q_hi = ao_r3(c, qh, bh, q3, b3);
     if (R == 2) return q_hi;
     double ql = 0.0;
     for (int j = 0; j < nl; ++j) ql += w_lo[j] * f[1 + j];
-    double bl = ao_beta(c, K_lo, f + 1, nl, mean, c->ao_const[1]);
+    double bl = ao_beta(c, K_lo, f + 1, nl, mean, c->ao_const[1], c->ao_scale[1]);
     double q_lo = ao_r3(c, ql, bl, q3, b3);
     double ghi = c->ao_gamma_hi;
     double vh = ghi / pow(c->eps + bh, (double)c->p), vl = (1.0 - ghi) / pow(c->eps + bl, (double)c->p);

@@ -357,6 +357,8 @@ def _ao_decimal(R: int, ell_s: str, sigma_s: str, xs_s: str):
         out["w_" + key] = gp_weights(pts, xs, ell) if key != "3" else None
         Ks = covariance(pts, sigma)
         out["Kinv_" + key] = inverse(Ks)
+        with decimal.localcontext(_ctx()):
+            out["one_" + key] = sum((sum(row, Decimal(0)) for row in out["Kinv_" + key]), Decimal(0))   # 1^T K^-1 1
         lam, _ = jacobi_eigen(Ks)
         with decimal.localcontext(_ctx()):
             out["logdet_" + key] = sum((l.ln() for l in lam), Decimal(0))

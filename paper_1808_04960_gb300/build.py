@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpweno.so")
 SOURCES = ["api.cu", "stage_f32.cu", "stage_f64.cu", "gp_precompute.cpp", "noalloc.cu", "batch_f32.cu",
-           "batch_f64.cu"] + ["stage_%s_var%d.cu" % (t, v) for t in ("f32", "f64") for v in (1, 2, 3, 4, 5)]
+           "batch_f64.cu"] + ["stage_%s_var%d.cu" % (t, v) for t in ("f32", "f64") for v in (1, 2, 3, 4, 5, 8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

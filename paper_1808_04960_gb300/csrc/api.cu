@@ -162,6 +162,10 @@ gpweno_status gpweno_plan_create(gpweno_plan *out, int R, double ell_over_dx, co
                       dims->ndim - 1);
             return GPWENO_ERR_ARG;
         }
+        if (ext && (o.beta_mean || o.scheme || o.ao)) {
+            set_error("external (halo) sides are supported by the default scheme (beta_mean = 0, scheme = 0, ao = 0)");
+            return GPWENO_ERR_ARG;
+        }
         if (ext && dims->n[d] < R + 3) {
             set_error("dimension %d: a slab with external sides needs at least R+3 = %d cells, has %d", d, R + 3,
                       dims->n[d]);

@@ -874,8 +874,11 @@ __device__ __forceinline__ bool face_fdf(const T (&st)[2 * R + 2][NC], const Fac
 }
 
 // Scheme variants chosen at compile time: bit 0 the non-zero-mean smoothness
-// indicators, bit 1 the FD-Flux form, bit 2 GP-AO.
-constexpr int kVarMean = 1, kVarFdFlux = 2, kVarAo = 4;
+// indicators, bit 1 the FD-Flux form, bit 2 GP-AO; bit 3 is not a scheme change
+// but a grid with an external (halo) side, whose loaders read ghost layers from
+// halo buffers -- a separate instantiation so that the loaders of the others stay
+// as they are.
+constexpr int kVarMean = 1, kVarFdFlux = 2, kVarAo = 4, kVarSlab = 8;
 
 // Kernel parameter type of a variant's tables.
 template <typename T, int R, int VAR>

@@ -437,7 +437,7 @@ bool side_tables(dd q, int R, int xs2, double *w_sub, double *w_big, double *gam
 // alternating -- checked), the row sums Psum (zero for skew rows) and
 // log det K_N.
 bool eigen_factors(dd qs, int N, double *P, double *lambda, double *Ph, double *Psum, double *logdet, char *err,
-                   std::size_t errlen)
+                   std::size_t errlen, double *one_kinv_one = nullptr)
 {
     dd Ks[kMaxBig][kMaxBig], V[kMaxBig][kMaxBig];
     for (int a = 0; a < N; ++a)
@@ -453,6 +453,7 @@ bool eigen_factors(dd qs, int N, double *P, double *lambda, double *Ph, double *
                 order[b] = t;
             }
     double ld = 0.0;
+    dd ones = make(0.0);   // 1^T K^-1 1 = sum_h (v_h . 1)^2 / lambda_h
     for (int h = 0; h < N; ++h) {
         int e = order[h];
         dd lam = Ks[e][e];
@@ -463,8 +464,14 @@ bool eigen_factors(dd qs, int N, double *P, double *lambda, double *Ph, double *
         lambda[h] = to_d(lam);
         ld += std::log(lambda[h]);
         dd rs = div(make(1.0), sqrt_dd(lam));
-        for (int j = 0; j < N; ++j) P[h * N + j] = to_d(mul(V[j][e], rs));
+        dd vs = make(0.0);
+        for (int j = 0; j < N; ++j) {
+            P[h * N + j] = to_d(mul(V[j][e], rs));
+            vs = add(vs, V[j][e]);
+        }
+        ones = add(ones, div(mul(vs, vs), lam));
     }
+    if (one_kinv_one) *one_kinv_one = to_d(ones);
     if (logdet) *logdet = ld;
     // half form, descending lambda, with the symmetric/skew alternation checked
     for (int k = 0; k < N; ++k) {
@@ -576,13 +583,29 @@ int ao_precompute(int R, double ell, double sigma, AoTables *out, char *err, std
         std::snprintf(err, errlen, "a GP-AO stencil covariance is not positive definite in double-double");
         return 2;
     }
-    double lam[kMaxBig];
-    if (!eigen_factors(qs, 2 * R + 1, out->P_hi, lam, out->Ph_hi, out->Psum_hi, &out->logdet_hi, err, errlen))
+    // Stencils of different size are compared through the data-fit term per unit of that of
+    // constant data: beta_N = f^T K_N^-1 f / (1^T K_N^-1 1), so that smooth data give every
+    // stencil nearly the same indicator; dividing beta by 1^T K_N^-1 1 (double-double) scales the
+    // factors P by its inverse square root.
+    double lam[kMaxBig], one_hi = 1.0, one_lo = 1.0, one_3 = 1.0;
+    if (!eigen_factors(qs, 2 * R + 1, out->P_hi, lam, out->Ph_hi, out->Psum_hi, &out->logdet_hi, err, errlen,
+                       &one_hi))
         return 2;
     if (R == 3 && !eigen_factors(qs, 2 * R - 1, out->P_lo, lam, out->Ph_lo, out->Psum_lo, &out->logdet_lo, err,
-                                 errlen))
+                                 errlen, &one_lo))
         return 2;
-    if (!eigen_factors(qs, 3, out->P_3, lam, out->Ph_3, out->Psum_3, &out->logdet_3, err, errlen)) return 2;
+    if (!eigen_factors(qs, 3, out->P_3, lam, out->Ph_3, out->Psum_3, &out->logdet_3, err, errlen, &one_3)) return 2;
+    auto normalise = [](int N, double one, double *P, double *Ph, double *Psum) {
+        const double s = 1.0 / std::sqrt(one);
+        for (int k = 0; k < N * N; ++k) {
+            P[k] *= s;
+            Ph[k] *= s;
+        }
+        for (int h = 0; h < N; ++h) Psum[h] *= s;
+    };
+    normalise(2 * R + 1, one_hi, out->P_hi, out->Ph_hi, out->Psum_hi);
+    if (R == 3) normalise(2 * R - 1, one_lo, out->P_lo, out->Ph_lo, out->Psum_lo);
+    normalise(3, one_3, out->P_3, out->Ph_3, out->Psum_3);
     return 0;
 }
 

@@ -98,6 +98,9 @@ gpweno_status launch_stage_f64_var2(gpweno_plan p, const StageIO &io, cudaStream
 gpweno_status launch_stage_f64_var3(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64_var4(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_stage_f64_var5(gpweno_plan p, const StageIO &io, cudaStream_t st);
+// grids with an external (halo) side: kVarSlab = 8
+gpweno_status launch_stage_f32_var8(gpweno_plan p, const StageIO &io, cudaStream_t st);
+gpweno_status launch_stage_f64_var8(gpweno_plan p, const StageIO &io, cudaStream_t st);
 gpweno_status launch_max_rate_f32(gpweno_plan p, const void *U, cudaStream_t st);
 gpweno_status launch_max_rate_f64(gpweno_plan p, const void *U, cudaStream_t st);
 gpweno_status launch_batch_stage_f32(gpweno_plan batch, int stage, void *const *U, void *const *scratch,

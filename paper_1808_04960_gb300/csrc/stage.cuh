@@ -184,9 +184,38 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     using RG = Ring2D<R, NT>;
     constexpr int G = RG::G, ROWS = RG::ROWS, STRIDE = RG::STRIDE;
     constexpr int NS = 2 * R + 2;
-    T *ring = smem;                              // [ROWS][NC][STRIDE]
-    T *FA = smem + ROWS * NC * STRIDE;           // [NC][NT]  x-face A = F_{s+1/2} - F(U_s)
-    T *FB = FA + NC * NT;                        // [NC][NT]  x-face B = F(U_{s+1}) - F(U_s)
+    // FP32 2D kernel: the four components of a ring element and of a staged face flux sit side
+    // by side (one 16-byte shared load per stencil cell or face flux); otherwise one array per
+    // component.  The one-site loop (batches), the FD-Flux form and GP-AO keep the per-component
+    // arrays: there the aligned register quads of 16-byte loads cost spills.
+    constexpr bool VEC = std::is_same<T, float>::value && NC == 4 && !ONE_SITE && (VAR & (kVarFdFlux | kVarAo)) == 0;
+    T *ring = smem;                              // [ROWS][NC][STRIDE], or [ROWS][STRIDE][4] (VEC)
+    T *FA = smem + ROWS * NC * STRIDE;           // [NC][NT] (or [NT][4]): x-face A = F_{s+1/2} - F(U_s)
+    T *FB = FA + NC * NT;                        // [NC][NT] (or [NT][4]): x-face B = F(U_{s+1}) - F(U_s)
+    // offset of component c of element col in the ring row starting at `base`, and of a face flux
+    auto ro = [](int base, int col, int c) { return VEC ? base + col * 4 + c : base + c * STRIDE + col; };
+    auto fo = [](int t, int c) { return VEC ? t * 4 + c : c * NT + t; };
+    // the NC values of element col of a ring row (VEC: one 16-byte load)
+    auto ring_elem = [&](int base, int col, T (&v)[NC]) {
+        if constexpr (VEC) {
+            const float4 q = *reinterpret_cast<const float4 *>(ring + base + col * 4);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = ring[base + c * STRIDE + col];
+        }
+    };
+    auto stage_face = [&](T *F, int t, const T (&v)[NC]) {
+        if constexpr (VEC) {
+            *reinterpret_cast<float4 *>(F + t * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c * NT + t] = v[c];
+        }
+    };
     const int tid = threadIdx.x;
     const int nx = a.n[0], ny = a.n[1];
     const long plane = a.cstride;
@@ -198,13 +227,13 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
 
     auto load_row = [&](int g) {
         T *dst = ring + RG::slot(g) * (NC * STRIDE);
-        if (NC == 4 && a.slab_dim == 1 && ((g < 0 && a.ext[0]) || (g >= ny && a.ext[1]))) {
+        if ((VAR & kVarSlab) != 0 && NC == 4 && a.slab_dim == 1 && ((g < 0 && a.ext[0]) || (g >= ny && a.ext[1]))) {
             // a ghost row of an external side: from the halo buffer [nc][G][nx]
             const T *src = g < 0 ? a.halo[0] + (long)(g + G) * nx : a.halo[1] + (long)(g - ny) * nx;
             for (int col = tid; col < rowlen; col += NT) {
                 const int gx = bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * STRIDE + col, src + (long)c * G * nx + gx);
+                for (int c = 0; c < NC; ++c) cp_async_elem(dst + ro(0, col, c), src + (long)c * G * nx + gx);
             }
             return;
         }
@@ -213,7 +242,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         for (int col = tid; col < rowlen; col += NT) {
             const int gx = bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * STRIDE + col, src + c * plane + gx);
+            for (int c = 0; c < NC; ++c) cp_async_elem(dst + ro(0, col, c), src + c * plane + gx);
         }
     };
 
@@ -260,6 +289,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             for (int pass = 0; pass < 2; ++pass) {
                 if (pass == 0 ? !do_y : !do_x) continue;
                 // stencil element (q, c): ring + off[q] + comp[c] * STRIDE, normal-first
+                static_assert(!VEC, "the one-site loop keeps one array per component");
                 int off[NS];
 #pragma unroll
                 for (int q = 0; q < NS; ++q)
@@ -294,11 +324,8 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                         Bp[c] = Bc[c];
                     }
                 } else {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        FA[c * NT + tid] = An[c];
-                        FB[c * NT + tid] = Bn[c];
-                    }
+                    stage_face(FA, tid, An);
+                    stage_face(FB, tid, Bn);
                 }
             }
         } else {
@@ -307,10 +334,17 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 T st[NS][NC];
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
-                    const T *row = ring + RG::slot(s - R + q) * (NC * STRIDE) + G + tid;
+                    const int base = RG::slot(s - R + q) * (NC * STRIDE);
                     // normal-first for a y-face: (rho, rho v, rho u, [rho w], E)
+                    if constexpr (VEC) {
+                        T v[NC];
+                        ring_elem(base, G + tid, v);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) st[q][c] = row[(c == 1 ? 2 : (c == 2 ? 1 : c)) * STRIDE];
+                        for (int c = 0; c < NC; ++c) st[q][c] = v[c == 1 ? 2 : (c == 2 ? 1 : c)];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) st[q][c] = ring[ro(base, G + tid, c == 1 ? 2 : (c == 2 ? 1 : c))];
+                    }
                 }
                 T An[NC], Bn[NC];
                 ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
@@ -334,34 +368,51 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             }
             // ---- x-faces of output row r ----------------------------------
             if (out_row && tid < Wc + 5) {
-                const T *row = ring + RG::slot(r) * (NC * STRIDE) + tid;
+                const int base = RG::slot(r) * (NC * STRIDE);
                 T st[NS][NC];
 #pragma unroll
-                for (int q = 0; q < NS; ++q)
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) st[q][c] = row[c * STRIDE + q];
+                for (int q = 0; q < NS; ++q) ring_elem(base, tid + q, st[q]);
                 T An[NC], Bn[NC];
                 ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    FA[c * NT + tid] = An[c];
-                    FB[c * NT + tid] = Bn[c];
-                }
+                stage_face(FA, tid, An);
+                stage_face(FB, tid, Bn);
             }
         }
         __syncthreads();
         // ---- divergence and stage combination -------------------------
         if (out_row && col_ok) {
-            const T *urow = ring + RG::slot(r) * (NC * STRIDE) + G + tid;
+            const int ubase = RG::slot(r) * (NC * STRIDE);
+            T un4[NC];
+            if constexpr (VEC) {
+                if (a.u0_is_stencil) ring_elem(ubase, G + tid, un4);
+            }
+            // x-faces t = tid..tid+5 are s' = x-3..x+2 around cell x = x0 + tid; the flux jumps
+            // dF_k = A_{k+1} - A_k + B_k across the five cells around x (VEC: all components
+            // from 16-byte loads, rolling over k; otherwise one component at a time)
+            T dxk[VEC ? 5 : 1][NC];
+            if constexpr (VEC) {
+                float4 q = *reinterpret_cast<const float4 *>(FA + tid * 4);
+                T prev[NC] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    q = *reinterpret_cast<const float4 *>(FA + (tid + k + 1) * 4);
+                    const float4 w = *reinterpret_cast<const float4 *>(FB + (tid + k) * 4);
+                    const T cur[NC] = {q.x, q.y, q.z, q.w}, b[NC] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        dxk[k][c] = cur[c] - prev[c] + b[c];
+                        prev[c] = cur[c];
+                    }
+                }
+            }
             T res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                // x-faces t = tid..tid+5 are s' = x-3..x+2 around cell x = x0 + tid
-                const T *fa = FA + c * NT + tid;
-                const T *fb = FB + c * NT + tid;
                 T dx[5];
 #pragma unroll
-                for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
+                for (int k = 0; k < 5; ++k)
+                    dx[k] = VEC ? dxk[VEC ? k : 0][c]
+                                : FA[fo(tid + k + 1, c)] - FA[fo(tid + k, c)] + FB[fo(tid + k, c)];
                 const T divx = flux_divergence<T, VAR>(dx[0], dx[1], dx[2], dx[3], dx[4]);
                 const T divy = flux_divergence<T, VAR>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
                 const T L = -fma(divx, idx[0], divy * idx[1]);
@@ -369,7 +420,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                     a.out[c * plane + cell] = L;
                     res[c] = L;
                 } else {
-                    const T un = a.u0_is_stencil ? urow[c * STRIDE] : u0[c];
+                    const T un = a.u0_is_stencil ? (VEC ? un4[c] : ring[ro(ubase, G + tid, c)]) : u0[c];
                     res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt);
                 }
             }
@@ -542,8 +593,9 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
         constexpr int G = R + 3;
         T *dst = ring + RZ::slot(g) * (NC * NT) + tid;
         long ccs = cs;
-        const T *src = (a.slab_dim == 2 ? layer_src<T>(a, a.U, g, nz, a.per[2], plane, G, ccs)
-                                        : a.U + (long)bc_map(g, nz, a.per[2]) * plane) + col;
+        const T *src = ((VAR & kVarSlab) != 0 && a.slab_dim == 2 ? layer_src<T>(a, a.U, g, nz, a.per[2], plane, G, ccs)
+                                                                 : a.U + (long)bc_map(g, nz, a.per[2]) * plane) +
+                       col;
 #pragma unroll
         for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * NT, src + c * ccs);
     };
@@ -680,8 +732,9 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
         const int Wc = min(a.W, nx - x0);
         for (int col = tid; col < Wc + 2 * G; col += NT) {
             long cs = nx;
-            const T *src = a.slab_dim == 0 ? layer_src<T>(a, a.U, x0 - G + col, nx, a.per[0], 1, G, cs)
-                                           : a.U + bc_map(x0 - G + col, nx, a.per[0]);
+            const T *src = (VAR & kVarSlab) != 0 && a.slab_dim == 0
+                               ? layer_src<T>(a, a.U, x0 - G + col, nx, a.per[0], 1, G, cs)
+                               : a.U + bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
             for (int c = 0; c < NC; ++c) row[c * STRIDE + col] = src[c * cs];
         }

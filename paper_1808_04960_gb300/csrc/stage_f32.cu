@@ -8,8 +8,10 @@ namespace gpweno {
 
 gpweno_status launch_stage_f32(gpweno_plan p, const StageIO &io, cudaStream_t st)
 {
-    const int var = (p->opts.beta_mean ? kVarMean : 0) | (p->opts.scheme ? kVarFdFlux : 0) | (p->opts.ao ? kVarAo : 0);
+    const int var = (p->opts.beta_mean ? kVarMean : 0) | (p->opts.scheme ? kVarFdFlux : 0) | (p->opts.ao ? kVarAo : 0) |
+                    (has_external_side(p) ? kVarSlab : 0);
     switch (var) {
+    case kVarSlab: return launch_stage_f32_var8(p, io, st);
     case kVarMean: return launch_stage_f32_var1(p, io, st);
     case kVarFdFlux: return launch_stage_f32_var2(p, io, st);
     case kVarFdFlux | kVarMean: return launch_stage_f32_var3(p, io, st);

@@ -102,3 +102,25 @@ def test_batch_rejects_mixed_dtype():
     p2 = gpweno.Plan(2, 12.0, U.shape[1:], meta["dx"], meta["bc"], dtype="f64")
     with pytest.raises(gpweno.GpwenoError):
         gpweno.BatchPlan([p1, p2])
+
+
+@pytest.mark.parametrize("cand", [(128, 4, 0, 8, 1), (128, 2, 64, 24, 2), (256, 2, 96, 8, 2), (256, 1, 0, 24, 1),
+                                  (128, 3, 96, 24, 1)])
+def test_batch_tile_shapes_bitwise(tmp_path, cand):
+    """Every tile shape the autotuner searches (block, CTAs per SM, strip-width cap, fewest
+    segment rows, CTA shares per slot) gives the same bits: the schedule changes which CTA
+    evaluates a face, never the face's arithmetic."""
+    from paper_1808_04960_gb300 import autotune
+    assert cand in autotune.CANDIDATES
+    insts = make_instances(10, seed=31)
+    _, ref, _, batch, _ = run_both(insts, "f32", steps=2)
+    sig = batch.info()["signature"]
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{sig} " + " ".join(str(x) for x in cand) + "\n")
+    _, Ub, _, b2, _ = run_both(insts, "f32", steps=2, tune_cache=str(cache))
+    info = b2.info()
+    assert (info["block"], info["ctas_per_sm"], info["min_rows"], info["ctas_per_slot"]) == \
+        (cand[0], cand[1], cand[3], cand[4])
+    assert info["strip_width_cap"] == (cand[2] if cand[2] else cand[0] - 5)
+    for a, b in zip(ref, Ub):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())

@@ -159,7 +159,7 @@ def test_dd_recon_tables_match_oracle(lib, R, ell):
 @pytest.mark.parametrize("R,ell", [(2, 12.0), (3, 12.0), (3, 6.0)])
 def test_dd_ao_tables_match_oracle(lib, R, ell):
     """GP-AO tables: the library's double-double weights of the three stencil sizes and the
-    K_N(sigma) factors (P^T P = K_N^-1) against the oracle's 100-digit ones."""
+    K_N(sigma) factors (P^T P = K_N^-1 / 1^T K_N^-1 1) against the oracle's 100-digit ones."""
     t = gpweno.ao_tables(R, ell, 3.0)
     for side, xs in ((0, 0.5), (1, -0.5)):
         o = OT.ao_tables(R, ell, 3.0, xs)
@@ -169,8 +169,13 @@ def test_dd_ao_tables_match_oracle(lib, R, ell):
             np.testing.assert_allclose(t["w_lo"][side], o["w_lo"], rtol=0, atol=1e-13 * np.abs(o["w_lo"]).max())
     o = OT.ao_tables(R, ell, 3.0, 0.5)
     keys = ("hi", "lo", "3") if R == 3 else ("hi", "3")
+    dec = OT._ao_decimal(R, str(OT._D(ell)), str(OT._D(3.0)), str(OT._D(0.5)))
     for k in keys:
         P = t["P_" + k]
-        np.testing.assert_allclose(P.T @ P, o["Kinv_" + k], rtol=0, atol=1e-11 * np.abs(o["Kinv_" + k]).max())
+        # the factors of the size-normalised indicator: P^T P = K_N^-1 / (1^T K_N^-1 1), the sum
+        # taken in the oracle's decimal arithmetic (its entries cancel)
+        one = float(sum(sum(row) for row in dec["Kinv_" + k]))
+        Kn = o["Kinv_" + k] / one
+        np.testing.assert_allclose(P.T @ P, Kn, rtol=0, atol=1e-11 * np.abs(Kn).max())
     with pytest.raises(gpweno.GpwenoError):
         gpweno.ao_tables(1, 12.0, 3.0)
