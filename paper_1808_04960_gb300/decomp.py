@@ -7,9 +7,9 @@ disc_fd reaches G cells), and a common CFL time step takes one max-reduction
 of the three per-direction wavespeed maxima per step.  The paper's solver is
 parallelized the same way across CPU cores (Section 5; its vortex timings of
 Section 6.2 ran on four cores); here each slab is one GPU and the transport is
-torch.distributed (NCCL on GPUs, gloo on CPU tensors).  The cut sides of a slab are GPWENO_BC_EXTERNAL
-sides of its plan; the outer sides keep the grid's boundary condition
-(periodic grids close the ring of slabs).
+torch.distributed (NCCL on GPUs, gloo on CPU tensors).  The cut sides of a slab
+are GPWENO_BC_EXTERNAL sides of its plan; the outer sides keep the grid's
+boundary condition (periodic grids close the ring of slabs).
 
 Batches.  Independent instances are split over ranks by estimated cost, with
 no exchange at all.
