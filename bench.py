@@ -454,6 +454,8 @@ def run_batch(args, stream, rank=0, ws=1):
     costs = [decomp.instance_cost(i["nx"], i["ny"], i["R"]) for i in insts]
     parts, loads = decomp.shard_instances(costs, ws)
     mine = [insts[k] for k in parts[rank]]
+    if not mine:
+        raise RuntimeError(f"{ws} ranks for {len(insts)} batch instances: rank {rank} has none")
     cache = os.path.join(ROOT, "paper_1808_04960_gb300", "tune_cache.txt")
 
     def build(dtype):

@@ -22,8 +22,8 @@ from . import gpweno
 # (block, CTAs per SM) pairs the register budget allows, then the tile shapes
 BLOCKS = ((128, 2), (128, 3), (128, 4), (256, 1), (256, 2))
 WIDTH_CAPS = (0, 64, 96)         # 0: the widest strip the block allows (block - 5 columns)
-MIN_ROWS = (8, 24)
-SHARES_PER_SLOT = (1, 2)
+MIN_ROWS = (4, 8, 16, 24)
+SHARES_PER_SLOT = (1, 2, 3, 4)
 CANDIDATES = tuple((b, c, w, r, o) for (b, c), w, r, o in itertools.product(BLOCKS, WIDTH_CAPS, MIN_ROWS,
                                                                             SHARES_PER_SLOT))
 
