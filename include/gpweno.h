@@ -291,19 +291,21 @@ gpweno_status gpweno_ao_tables(int R, double ell_over_dx, double sigma_over_dx, 
 gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 
 /* Batched 2D stepping (same per-face scheme as gpweno_rk3_step): one
- * persistent launch per RK stage serves n independent 2D plans of possibly
+ * launch per RK stage serves n independent 2D plans of possibly
  * different grid size, R, l/dx, sigma, face flux, candidates and boundary
  * conditions (all plans must share dtype and device and use beta_mean = 0,
  * scheme = 0 and ao = 0, else GPWENO_ERR_ARG; at most 12 distinct table sets
  * per radius).  The host cuts every
  * instance into strips and row segments and hands each CTA a contiguous run of
- * segments of equal estimated cost.  The batch refers to the member plans,
+ * segments of equal estimated cost (by default 8 CTAs per resident CTA slot,
+ * so that the hardware scheduler evens out the estimate's misses).  The batch
+ * refers to the member plans,
  * which must outlive it.  tune_cache: NULL, or the path of a text file of
  * lines "<signature hex> <block 128|256> <ctas per SM>" (written by
  * paper_1808_04960_gb300/autotune.py); a line whose signature matches this
  * batch overrides the built-in block-size choice; a line may add three more
  * fields "<strip width cap (0 = as the block allows)> <fewest rows of a segment
- * that does not end its strip> <CTA shares per resident slot (1..4)>" (the
+ * that does not end its strip> <CTA shares per resident slot (1..16)>" (the
  * tile shapes the autotuner searches).  Allocates its schedule and descriptor
  * arrays on the device. */
 gpweno_status gpweno_plan_batch(gpweno_plan *out_batch, const gpweno_plan *plans, int n, const char *tune_cache);

@@ -23,7 +23,7 @@ from . import gpweno
 BLOCKS = ((128, 2), (128, 3), (128, 4), (256, 1), (256, 2))
 WIDTH_CAPS = (0, 64, 96)         # 0: the widest strip the block allows (block - 5 columns)
 MIN_ROWS = (4, 8, 16, 24)
-SHARES_PER_SLOT = (1, 2, 3, 4)
+SHARES_PER_SLOT = (1, 2, 3, 4, 6, 8, 12, 16)
 CANDIDATES = tuple((b, c, w, r, o) for (b, c), w, r, o in itertools.product(BLOCKS, WIDTH_CAPS, MIN_ROWS,
                                                                             SHARES_PER_SLOT))
 

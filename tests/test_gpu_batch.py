@@ -105,7 +105,7 @@ def test_batch_rejects_mixed_dtype():
 
 
 @pytest.mark.parametrize("cand", [(128, 4, 0, 8, 1), (128, 2, 64, 24, 2), (256, 2, 96, 8, 2), (256, 1, 0, 24, 1),
-                                  (128, 3, 96, 24, 1)])
+                                  (128, 3, 96, 24, 1), (128, 4, 0, 16, 4), (128, 4, 64, 4, 16)])
 def test_batch_tile_shapes_bitwise(tmp_path, cand):
     """Every tile shape the autotuner searches (block, CTAs per SM, strip-width cap, fewest
     segment rows, CTA shares per slot) gives the same bits: the schedule changes which CTA
