@@ -1,9 +1,9 @@
-// Batched 2D stepping: one persistent launch per SSP-RK3 stage for many
-// independent instances of uneven size, radius R and length scales.
+// Batched 2D stepping: one launch per SSP-RK3 stage for many independent
+// instances of uneven size, radius R and length scales.
 //
 // The host flattens every instance into strips (as the single-instance
-// kernel does) and cuts the strips' rows into segments so that each CTA gets
-// an equal share of the estimated cost (face work grows with R and with the
+// kernel does) and cuts the strips' rows into segments so that each CTA share
+// (several per resident slot) gets an equal part of the estimated cost (face work grows with R and with the
 // number of 32-lane warps a strip keeps busy; every segment pays five
 // warm-up y-face rows).  A CTA walks its contiguous run of segments and, per
 // segment, dispatches on the instance's R to the same segment routine the
