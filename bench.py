@@ -444,7 +444,7 @@ def run_batch(args, stream, rank=0, ws=1):
     """Batched workload: `--batch-count` seeded 2D instances (n_x, n_y log-uniform on [64, 1024],
     R in {1,2,3}, l/dx in {6,12,24}, half four-quadrant, half vortex), per-instance CFL dt.
     With N ranks the instances are split over the ranks by estimated cost (no exchange: they are
-    independent), each rank one persistent launch per RK stage for its share.  FP32 under a CUDA
+    independent), each rank one launch per RK stage for its share.  FP32 under a CUDA
     graph against per-instance launches and against the FP64 batch; the FP32 states' error
     against the FP64 batch after the same steps."""
     import torch
@@ -517,12 +517,17 @@ def run_batch(args, stream, rank=0, ws=1):
     ms_u = max_over_ranks(e[0].elapsed_time(e[1]), ws) / args.batch_steps
     nonphys = batch.flags()
     info = batch.info()
+    # ALU fraction on the method's operation count of each instance's radius, over all ranks' peaks
+    alu_peak, _ = alu_peak_flops()
+    flops_stage = sum(i["nx"] * i["ny"] * flops_per_cell_stage(i["R"]) for i in insts)
     out = {"workload": f"{len(insts)} seeded 2D instances, n_x,n_y log-uniform on [64,1024], R in {{1,2,3}}, "
                        "l/dx in {6,12,24}, four-quadrant/vortex, FP32, per-instance CFL 0.4 (fixed dt)",
            "instances": len(insts), "cells": cells, "steps": args.batch_steps,
            "value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
            "unbatched_value": cells * 3 / (ms_u * 1e-3), "unbatched_ms_per_step": ms_u,
            "speedup_vs_unbatched": ms_u / ms_b, "launches_per_step": 3,
+           "alu_frac": flops_stage * 3 / (ms_b * 1e-3) / (alu_peak * ws),
+           "flops_per_cell_stage_mean": flops_stage / cells,
            "unbatched_launches_per_step": 3 * len(insts), "schedule": info, "nonphysical_flag": nonphys,
            "sharding": {"ranks": ws, "instances_per_rank": [len(p) for p in parts],
                         "cost_share_max_over_mean": max(loads) / (sum(loads) / ws)}}
