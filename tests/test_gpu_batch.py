@@ -40,11 +40,6 @@ def make_instances(count, seed, nmin=16, nmax=300):
     return out
 
 
-def torch_sms():
-    import torch
-    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-
-
 def run_both(insts, dtype, steps=3, tune_cache=None):
     import torch
     tdt = torch.float32 if dtype == "f32" else torch.float64
@@ -79,7 +74,6 @@ def test_batch_bitwise_equals_single(dtype):
     assert info["grid"] >= 1 and info["segments"] >= len(insts)
     # built-in schedule (no tuning cache): 8 CTA shares per resident slot, 8-row minimum segments
     assert info["ctas_per_slot"] == 8 and info["min_rows"] == 8
-    assert info["grid"] <= 8 * info["ctas_per_sm"] * torch_sms()
 
 
 def test_batch_f64_matches_oracle():
