@@ -8,6 +8,7 @@
 #include <new>
 
 #include "plan.h"
+#include "trace.h"
 
 namespace gpweno {
 
@@ -346,6 +347,7 @@ gpweno_status rk3_sequence(gpweno_plan p, void *U, void *D, void *V1, void *V2, 
                            const double *dt_dev, bool want_rate, cudaStream_t st)
 {
     for (int k = 0; k < 3; ++k) {
+        TraceRange tr(stage_range_name(k));
         gpweno_status s = launch_stage(p, stage_io(k, U, D, V1, V2, lo, dt, dt_dev, want_rate), st);
         if (s != GPWENO_OK) return s;
     }
@@ -413,6 +415,7 @@ extern "C" {
 
 gpweno_status gpweno_rhs(gpweno_plan p, const void *U, void *dUdt, void *stream)
 {
+    TraceRange tr("gpweno_rhs");
     g_launches = 0;
     if (!p || p->is_batch || !U || !dUdt) {
         set_error("gpweno_rhs: invalid argument");
@@ -451,6 +454,7 @@ gpweno_status gpweno_set_halo(gpweno_plan p, const void *recv_lo, const void *re
 
 gpweno_status gpweno_halo_pack(gpweno_plan p, const void *state, void *send_lo, void *send_hi, void *stream)
 {
+    TraceRange tr("gpweno_halo_pack");
     g_launches = 0;
     const uintptr_t esz = p && p->opts.dtype == GPWENO_F32 ? 4 : 8;
     if (!p || p->is_batch || !state || (reinterpret_cast<uintptr_t>(state) % esz) != 0 ||
@@ -484,6 +488,7 @@ gpweno_status gpweno_halo_pack(gpweno_plan p, const void *state, void *send_lo, 
 gpweno_status gpweno_rk3_stage(gpweno_plan p, int stage, void *U, void *scratch, double dt, void *dt_dev,
                                void *stream)
 {
+    TraceRange tr(stage_range_name(stage));
     g_launches = 0;
     if (!p || p->is_batch || !U || !scratch || stage < 0 || stage > 2) {
         set_error("gpweno_rk3_stage: invalid argument");
@@ -549,6 +554,7 @@ gpweno_status gpweno_dt_from_rates(gpweno_plan p, const void *rates, double cfl,
 
 gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, void *dt_dev, void *stream)
 {
+    TraceRange tr("gpweno_rk3_step");
     g_launches = 0;
     if (!p || p->is_batch || !U || !scratch) {
         set_error("gpweno_rk3_step: invalid argument");
@@ -585,6 +591,7 @@ gpweno_status gpweno_rk3_step(gpweno_plan p, void *U, void *scratch, double dt, 
 
 gpweno_status gpweno_cfl_dt(gpweno_plan p, const void *U, double cfl, void *dt_dev, void *stream)
 {
+    TraceRange tr("gpweno_cfl_dt");
     g_launches = 0;
     if (!p || p->is_batch || !U || !dt_dev || !(cfl > 0.0)) {
         set_error("gpweno_cfl_dt: invalid argument");
@@ -670,6 +677,7 @@ gpweno_status gpweno_plan_batch(gpweno_plan *out, const gpweno_plan *plans, int 
 gpweno_status gpweno_batch_rk3_step(gpweno_plan b, void *const *U, void *const *scratch, const void *dt_dev,
                                     void *stream)
 {
+    TraceRange tr("gpweno_batch_rk3_step");
     g_launches = 0;
     if (!b || !b->is_batch || !U || !scratch || !dt_dev) {
         set_error("gpweno_batch_rk3_step: invalid argument");
@@ -684,6 +692,7 @@ gpweno_status gpweno_batch_rk3_step(gpweno_plan b, void *const *U, void *const *
     cudaStream_t st = (cudaStream_t)stream;
     const double *dt = static_cast<const double *>(dt_dev);
     for (int stage = 0; stage < 3; ++stage) {
+        TraceRange trs(stage_range_name(stage));
         gpweno_status s = b->opts.dtype == GPWENO_F32 ? launch_batch_stage_f32(b, stage, U, scratch, dt, st)
                                                       : launch_batch_stage_f64(b, stage, U, scratch, dt, st);
         if (s != GPWENO_OK) return s;

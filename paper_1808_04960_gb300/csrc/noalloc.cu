@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "plan.h"
+#include "trace.h"
 
 namespace gpweno {
 namespace {
@@ -103,6 +104,7 @@ using namespace gpweno;
 
 extern "C" gpweno_status gpweno_rk3_step_noalloc(gpweno_plan p, void *U, double dt, void *stream)
 {
+    TraceRange tr("gpweno_rk3_step_noalloc");
     reset_launch_count();
     if (!p || p->is_batch || !U) {
         set_error("gpweno_rk3_step_noalloc: invalid argument");

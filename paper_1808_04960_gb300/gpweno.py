@@ -172,6 +172,14 @@ class Plan:
         self.R = int(R)
         self.dtype = {"f32": torch.float32, "f64": torch.float64}[dtype]
         self.cfl = float(cfl)
+        # creation parameters (what a checkpoint must agree with to resume on this plan)
+        self.params = {"R": self.R, "ell_over_dx": float(ell_over_dx), "shape": list(self.shape),
+                       "dx": [float(dx[a]) for a in range(self.ndim)],
+                       "bc": [[str(bc[a][0]), str(bc[a][1])] for a in range(self.ndim)], "gamma": float(gamma),
+                       "sigma_over_dx": float(sigma_over_dx), "eps": float(eps), "p": int(p), "dtype": dtype,
+                       "cfl": self.cfl, "flux": flux, "beta_mean": bool(beta_mean), "candidates": candidates,
+                       "scheme": scheme, "ao": bool(ao), "ao_gamma_hi": float(ao_gamma_hi),
+                       "ao_gamma_lo": float(ao_gamma_lo)}
         dims = Dims()
         dims.ndim = self.ndim
         n_xyz = list(reversed(self.shape))

@@ -162,3 +162,49 @@ def test_shard_instances_cover_and_balance(world):
     for p, load in zip(parts, loads):
         assert abs(sum(costs[i] for i in p) - load) < 1e-6 * load
     assert max(loads) - sum(costs) / world < max(costs)         # greedy bound
+
+
+def _rank_leaves(rank, ws, port, out):
+    """Rank 1 leaves between steps (after the first exchange, before the second) without
+    tearing down its process group; rank 0's next exchange must end in an error, not a hang."""
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws, timeout=datetime.timedelta(seconds=10))
+    G, shape = 5, (4, 12, 8)
+    send = [torch.full((shape[0], G, shape[2]), float(rank)) for _ in range(2)]
+    recv = [torch.zeros((shape[0], G, shape[2])) for _ in range(2)]
+    lo = hi = 1 - rank                       # two ranks on a periodic ring
+    decomp.halo_exchange(send[0], send[1], recv[0], recv[1], lo, hi)
+    out[(rank, "first")] = float(recv[0][0, 0, 0])
+    if rank == 1:
+        os._exit(0)                          # leaves without a word, none of its work in flight
+    t0 = time.time()
+    try:
+        decomp.halo_exchange(send[0], send[1], recv[0], recv[1], lo, hi)
+        out[(rank, "second")] = "completed"
+    except Exception as e:                   # noqa: BLE001 - the transport's own error type
+        out[(rank, "second")] = f"error: {type(e).__name__}"
+    out[(rank, "seconds")] = time.time() - t0
+    os._exit(0)
+
+
+def test_exchange_with_a_departed_rank_fails_on_the_host():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with mp.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_rank_leaves, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(60)
+        alive = [p.is_alive() for p in procs]
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+        res = dict(out)
+    assert not any(alive), "a rank hung"
+    assert res[(0, "first")] == 1.0 and res[(1, "first")] == 0.0
+    assert str(res[(0, "second")]).startswith("error"), res
+    assert res[(0, "seconds")] < 30
