@@ -101,6 +101,55 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// Bounds-checked build (-DGPWENO_CHECKED; the tests build it as a library of its own): every
+// shared-memory and global access of the stage kernels is first checked against the extent of
+// its array; a violation sets bit `site` of the plan's flag word and skips the access (a read
+// yields zero).  The default build compiles the checks away.
+#ifdef GPWENO_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+enum CheckSite {
+    kChkRingWrite = 1,   // staging copy into the shared ring (2D, xy-planes)
+    kChkStateRead = 2,   // global source of a staging copy (stage state or halo buffer)
+    kChkRingRead = 3,    // stencil or U^n read from the ring
+    kChkFaceWrite = 4,   // staged x-face fluxes
+    kChkFaceRead = 5,
+    kChkEpiRead = 6,     // U^n, increment, remainder or partial L of an output cell
+    kChkEpiWrite = 7,    // stage outputs
+    kChkZRing = 8,       // z kernel: shared ring
+    kChkZState = 9,      // z kernel: staging source
+    kChkLine = 10,       // 1D kernel: shared row and face arrays
+    kChkLineState = 11   // 1D kernel: staging source
+};
+
+__device__ __forceinline__ bool chk(long long i, long long n, int site, int *flags)
+{
+    if constexpr (kChecked) {
+        if (i < 0 || i >= n) {
+            atomicOr(flags, 1 << site);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Checked build: does p point into the stage state (ext_state elements) or into a registered
+// halo buffer (ext_halo elements each)?
+template <typename T>
+__device__ __forceinline__ bool src_ok(const StageArgs<T> &a, const T *p, long ext_state, long ext_halo, int site)
+{
+    if constexpr (kChecked) {
+        const bool in = (p >= a.U && p < a.U + ext_state) ||
+                        (a.halo[0] != nullptr && p >= a.halo[0] && p < a.halo[0] + ext_halo) ||
+                        (a.halo[1] != nullptr && p >= a.halo[1] && p < a.halo[1] + ext_halo);
+        if (!in) atomicOr(a.flags, 1 << site);
+        return in;
+    }
+    return true;
+}
+
 // Ring geometry of the 2D kernel for radius R and block size NT.
 template <int R, int NT>
 struct Ring2D {
@@ -134,8 +183,10 @@ __device__ __forceinline__ T two_sum(T a, T b, T &e)
 // the cell, u0/din/lo the prefetched U^n, previous increment and remainder.
 // Returns the value whose wavespeed the CFL reduction sees (mode 2: U^{n+1}).
 template <typename T>
-__device__ __forceinline__ T stage_epilogue(const StageArgs<T> &a, long cell, T L, T u0, T din, T lo, T dt)
+__device__ __forceinline__ T stage_epilogue(const StageArgs<T> &a, long cell, T L, T u0, T din, T lo, T dt,
+                                            long extent)
 {
+    if (!chk(cell, extent, kChkEpiWrite, a.flags)) return L;
     if (a.mode == kModeRHS) {
         a.out[cell] = L;
         return L;
@@ -197,6 +248,15 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     auto fo = [](int t, int c) { return VEC ? t * 4 + c : c * NT + t; };
     // the NC values of element col of a ring row (VEC: one 16-byte load)
     auto ring_elem = [&](int base, int col, T (&v)[NC]) {
+        if constexpr (kChecked) {
+            const int first = VEC ? base + col * 4 : base + col, last = VEC ? first + 3 : first + (NC - 1) * STRIDE;
+            if (!chk(first, ROWS * NC * STRIDE, kChkRingRead, a.flags) ||
+                !chk(last, ROWS * NC * STRIDE, kChkRingRead, a.flags)) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) v[c] = T(0);
+                return;
+            }
+        }
         if constexpr (VEC) {
             const float4 q = *reinterpret_cast<const float4 *>(ring + base + col * 4);
             v[0] = q.x;
@@ -208,7 +268,10 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             for (int c = 0; c < NC; ++c) v[c] = ring[base + c * STRIDE + col];
         }
     };
+    // one ring element (checked build: in bounds or zero)
+    auto ring_at = [&](int i) -> T { return chk(i, ROWS * NC * STRIDE, kChkRingRead, a.flags) ? ring[i] : T(0); };
     auto stage_face = [&](T *F, int t, const T (&v)[NC]) {
+        if (!chk(t, NT, kChkFaceWrite, a.flags)) return;
         if constexpr (VEC) {
             *reinterpret_cast<float4 *>(F + t * 4) = make_float4(v[0], v[1], v[2], v[3]);
         } else {
@@ -225,6 +288,13 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     const int rowlen = Wc + 2 * G;
     const T idx[3] = {a.idx[0], a.idx[1], a.idx[2]};
 
+    // one staging copy (checked build: destination in the ring, source in the state or a halo)
+    auto stage_copy = [&](T *dst, const T *src) {
+        if (!chk(dst - ring, ROWS * NC * STRIDE, kChkRingWrite, a.flags) ||
+            !src_ok<T>(a, src, (long)NC * plane, (long)NC * G * nx, kChkStateRead))
+            return;
+        cp_async_elem(dst, src);
+    };
     auto load_row = [&](int g) {
         T *dst = ring + RG::slot(g) * (NC * STRIDE);
         if ((VAR & kVarSlab) != 0 && NC == 4 && a.slab_dim == 1 && ((g < 0 && a.ext[0]) || (g >= ny && a.ext[1]))) {
@@ -233,7 +303,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
             for (int col = tid; col < rowlen; col += NT) {
                 const int gx = bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) cp_async_elem(dst + ro(0, col, c), src + (long)c * G * nx + gx);
+                for (int c = 0; c < NC; ++c) stage_copy(dst + ro(0, col, c), src + (long)c * G * nx + gx);
             }
             return;
         }
@@ -242,7 +312,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         for (int col = tid; col < rowlen; col += NT) {
             const int gx = bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) cp_async_elem(dst + ro(0, col, c), src + c * plane + gx);
+            for (int c = 0; c < NC; ++c) stage_copy(dst + ro(0, col, c), src + c * plane + gx);
         }
     };
 
@@ -276,9 +346,10 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         const bool epi = out_row && col_ok && (a.mode == kModeIncrement || a.mode == kModeFinal);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            u0[c] = (epi && !a.u0_is_stencil) ? a.U0[c * plane + cell] : T(0);
-            din[c] = (epi && a.Din) ? a.Din[c * plane + cell] : T(0);
-            lov[c] = (epi && a.lo && a.mode == kModeFinal) ? a.lo[c * plane + cell] : T(0);
+            const bool in = !epi || chk(c * plane + cell, (long)NC * plane, kChkEpiRead, a.flags);
+            u0[c] = (epi && in && !a.u0_is_stencil) ? a.U0[c * plane + cell] : T(0);
+            din[c] = (epi && in && a.Din) ? a.Din[c * plane + cell] : T(0);
+            lov[c] = (epi && in && a.lo && a.mode == kModeFinal) ? a.lo[c * plane + cell] : T(0);
         }
 
         if constexpr (ONE_SITE) {
@@ -301,7 +372,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                     for (int c = 0; c < NC; ++c) {
                         // a y-face's normal is the second velocity: (rho, rho v, rho u, [rho w], E)
                         const int cc = pass == 0 ? (c == 1 ? 2 : (c == 2 ? 1 : c)) : c;
-                        st[q][c] = ring[off[q] + cc * STRIDE];
+                        st[q][c] = ring_at(off[q] + cc * STRIDE);
                     }
                 T An[NC], Bn[NC];
                 ok = face_eval<T, NC, R, VAR>(st, tb, An, Bn) && ok;
@@ -343,7 +414,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                         for (int c = 0; c < NC; ++c) st[q][c] = v[c == 1 ? 2 : (c == 2 ? 1 : c)];
                     } else {
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) st[q][c] = ring[ro(base, G + tid, c == 1 ? 2 : (c == 2 ? 1 : c))];
+                        for (int c = 0; c < NC; ++c) st[q][c] = ring_at(ro(base, G + tid, c == 1 ? 2 : (c == 2 ? 1 : c)));
                     }
                 }
                 T An[NC], Bn[NC];
@@ -380,7 +451,7 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
         }
         __syncthreads();
         // ---- divergence and stage combination -------------------------
-        if (out_row && col_ok) {
+        if (out_row && col_ok && chk(tid + 5, NT, kChkFaceRead, a.flags)) {
             const int ubase = RG::slot(r) * (NC * STRIDE);
             T un4[NC];
             if constexpr (VEC) {
@@ -417,11 +488,11 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
                 const T divy = flux_divergence<T, VAR>(Dy[0][c], Dy[1][c], Dy[2][c], Dy[3][c], Dy[4][c]);
                 const T L = -fma(divx, idx[0], divy * idx[1]);
                 if (NC == 5 || a.mode == kModePartial) {
-                    a.out[c * plane + cell] = L;
+                    if (chk(c * plane + cell, (long)NC * plane, kChkEpiWrite, a.flags)) a.out[c * plane + cell] = L;
                     res[c] = L;
                 } else {
-                    const T un = a.u0_is_stencil ? (VEC ? un4[c] : ring[ro(ubase, G + tid, c)]) : u0[c];
-                    res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt);
+                    const T un = a.u0_is_stencil ? (VEC ? un4[c] : ring_at(ro(ubase, G + tid, c))) : u0[c];
+                    res[c] = stage_epilogue<T>(a, c * plane + cell, L, un, din[c], lov[c], dt, (long)NC * plane);
                 }
             }
             if (NC == 4 && a.rate && a.mode == kModeFinal) {
@@ -597,7 +668,10 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
                                                                  : a.U + (long)bc_map(g, nz, a.per[2]) * plane) +
                        col;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) cp_async_elem(dst + c * NT, src + c * ccs);
+        for (int c = 0; c < NC; ++c)
+            if (chk(dst + c * NT - ring, RZ::ROWS * NC * NT, kChkZRing, a.flags) &&
+                src_ok<T>(a, src + c * ccs, NC * cs, (long)NC * G * plane, kChkZState))
+                cp_async_elem(dst + c * NT, src + c * ccs);
     };
     for (int g = s_begin - R; g <= s_begin + 1 + R; ++g) load_plane(g);
     cp_async_commit();
@@ -622,10 +696,11 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
         const bool epi = out && (a.mode == kModeIncrement || a.mode == kModeFinal);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            pv[c] = out ? a.P[c * cs + cell] : T(0);
-            u0[c] = (epi && !a.u0_is_stencil) ? a.U0[c * cs + cell] : T(0);
-            din[c] = (epi && a.Din) ? a.Din[c * cs + cell] : T(0);
-            lov[c] = (epi && a.lo && a.mode == kModeFinal) ? a.lo[c * cs + cell] : T(0);
+            const bool in = !out || chk(c * cs + cell, NC * cs, kChkEpiRead, a.flags);
+            pv[c] = (out && in) ? a.P[c * cs + cell] : T(0);
+            u0[c] = (epi && in && !a.u0_is_stencil) ? a.U0[c * cs + cell] : T(0);
+            din[c] = (epi && in && a.Din) ? a.Din[c * cs + cell] : T(0);
+            lov[c] = (epi && in && a.lo && a.mode == kModeFinal) ? a.lo[c * cs + cell] : T(0);
         }
         if (col_ok) {
             // normal-first for a z-face: (rho, rho w, rho u, rho v, E)
@@ -633,6 +708,7 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 const T *rowp = ring + RZ::slot(s - R + q) * (NC * NT) + tid;
+                if (!chk(rowp + 4 * NT - ring, RZ::ROWS * NC * NT, kChkZRing, a.flags)) rowp = ring;
                 st[q][0] = rowp[0];
                 st[q][1] = rowp[3 * NT];
                 st[q][2] = rowp[1 * NT];
@@ -656,13 +732,14 @@ __device__ __forceinline__ void stagez_segment(const StageArgs<T> &a, const Face
         }
         if (out) {
             const T *urow = ring + RZ::slot(r) * (NC * NT) + tid;
+            if (!chk(urow + 4 * NT - ring, RZ::ROWS * NC * NT, kChkZRing, a.flags)) urow = ring;
             T res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const T divz = flux_divergence<T, VAR>(Dz[0][c], Dz[1][c], Dz[2][c], Dz[3][c], Dz[4][c]);
                 const T L = fma(-divz, idx[2], pv[c]);
                 const T un = a.u0_is_stencil ? urow[c * NT] : u0[c];
-                res[c] = stage_epilogue<T>(a, c * cs + cell, L, un, din[c], lov[c], dt);
+                res[c] = stage_epilogue<T>(a, c * cs + cell, L, un, din[c], lov[c], dt, NC * cs);
             }
             if (a.rate && a.mode == kModeFinal) {
                 T rx, ry, rz;
@@ -736,10 +813,13 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
                                ? layer_src<T>(a, a.U, x0 - G + col, nx, a.per[0], 1, G, cs)
                                : a.U + bc_map(x0 - G + col, nx, a.per[0]);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) row[c * STRIDE + col] = src[c * cs];
+            for (int c = 0; c < NC; ++c)
+                if (chk(col, STRIDE, kChkLine, a.flags) &&
+                    src_ok<T>(a, src + c * cs, (long)NC * nx, (long)NC * G, kChkLineState))
+                    row[c * STRIDE + col] = src[c * cs];
         }
         __syncthreads();
-        if (tid < Wc + 5) {
+        if (tid < Wc + 5 && chk(tid + NS - 1, STRIDE, kChkLine, a.flags) && chk(tid, NT, kChkLine, a.flags)) {
             T st[NS][NC];
 #pragma unroll
             for (int q = 0; q < NS; ++q)
@@ -754,7 +834,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
             }
         }
         __syncthreads();
-        if (tid < Wc) {
+        if (tid < Wc && chk(tid + 5, NT, kChkLine, a.flags) && chk(G + tid, STRIDE, kChkLine, a.flags)) {
             T res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -765,11 +845,11 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(StageArgs<T> a, TablesFor<T
                 for (int k = 0; k < 5; ++k) dx[k] = fa[k + 1] - fa[k] + fb[k];
                 const T L = -flux_divergence<T, VAR>(dx[0], dx[1], dx[2], dx[3], dx[4]) * a.idx[0];
                 const long cell = (long)c * nx + x0 + tid;
-                const bool epi = a.mode != kModeRHS;
+                const bool epi = a.mode != kModeRHS && chk(cell, (long)NC * nx, kChkEpiRead, a.flags);
                 const T u0 = a.u0_is_stencil ? row[c * STRIDE + G + tid] : (epi ? a.U0[cell] : T(0));
                 const T din = (epi && a.Din) ? a.Din[cell] : T(0);
                 const T lov = (epi && a.lo && a.mode == kModeFinal) ? a.lo[cell] : T(0);
-                res[c] = stage_epilogue<T>(a, cell, L, u0, din, lov, dt);
+                res[c] = stage_epilogue<T>(a, cell, L, u0, din, lov, dt, (long)NC * nx);
             }
             if (a.rate && a.mode == kModeFinal) {
                 T ir = Num<T>::rcp(res[0]);
