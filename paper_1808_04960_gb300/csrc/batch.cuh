@@ -136,10 +136,14 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT)
         const BatchSeg sg = ssg;
         const T dt = sdt;
         const int tab = stab;
+        // FP32: the two-site row loop and interleaved layout of the single-instance kernel (no
+        // spills with all three radii in one kernel); FP64 keeps the one-site loop, whose smaller
+        // code spills less at 255 registers
+        constexpr bool kOneSite = sizeof(T) == 8;
         switch (sR) {
-        case 1: stage2d_segment<T, 1, NT, 4, 0, true>(sa, bt.t1[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
-        case 2: stage2d_segment<T, 2, NT, 4, 0, true>(sa, bt.t2[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
-        default: stage2d_segment<T, 3, NT, 4, 0, true>(sa, bt.t3[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        case 1: stage2d_segment<T, 1, NT, 4, 0, kOneSite>(sa, bt.t1[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        case 2: stage2d_segment<T, 2, NT, 4, 0, kOneSite>(sa, bt.t2[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
+        default: stage2d_segment<T, 3, NT, 4, 0, kOneSite>(sa, bt.t3[tab], sg.strip, sg.y0, sg.y1, smem, dt, rmx, rmy, ok); break;
         }
         // the segment ends with a barrier, so thread 0 may overwrite the shared arguments
     }

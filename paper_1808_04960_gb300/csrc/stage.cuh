@@ -226,8 +226,9 @@ __device__ __forceinline__ void rates2d(const T (&u)[4], T gam, const T (&idx)[3
 // NC = 4 (2D) or 5 (an xy-plane of a 3D grid).
 // ONE_SITE: evaluate the y- and x-face through one copy of the face routine (a
 // loop of two passes) instead of two inlined copies.  Two copies let the compiler
-// interleave the two independent faces (faster for the 2D kernel); one copy halves
-// the code, which pays where several radii share a kernel (batch) and in 3D.
+// interleave the two independent faces (faster for the 2D kernels, the FP32 batch
+// included); one copy halves the code, which pays in the FP64 batch (fewer spills
+// with three radii in one kernel) and in 3D.
 template <typename T, int R, int NT, int NC = 4, int VAR = 0, bool ONE_SITE = false>
 __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const FaceTables<T, R> &tb, int strip, int y0,
                                                 int y1, T *smem, T dt, T &rmx, T &rmy, bool &ok, long zoff = 0)
@@ -237,8 +238,8 @@ __device__ __forceinline__ void stage2d_segment(const StageArgs<T> &a, const Fac
     constexpr int NS = 2 * R + 2;
     // FP32 2D kernel: the four components of a ring element and of a staged face flux sit side
     // by side (one 16-byte shared load per stencil cell or face flux); otherwise one array per
-    // component.  The one-site loop (batches), the FD-Flux form and GP-AO keep the per-component
-    // arrays: there the aligned register quads of 16-byte loads cost spills.
+    // component.  The one-site loop (3D planes, FP64 batches), the FD-Flux form and GP-AO keep the
+    // per-component arrays: there the aligned register quads of 16-byte loads cost spills.
     constexpr bool VEC = std::is_same<T, float>::value && NC == 4 && !ONE_SITE && (VAR & (kVarFdFlux | kVarAo)) == 0;
     T *ring = smem;                              // [ROWS][NC][STRIDE], or [ROWS][STRIDE][4] (VEC)
     T *FA = smem + ROWS * NC * STRIDE;           // [NC][NT] (or [NT][4]): x-face A = F_{s+1/2} - F(U_s)
