@@ -285,9 +285,13 @@ gpweno_status gpweno_dt_from_rates(gpweno_plan plan, const void *rates, double c
 gpweno_status gpweno_ao_tables(int R, double ell_over_dx, double sigma_over_dx, double *w_hi, double *w_lo,
                                double *w3, double *P_hi, double *P_lo, double *P_3);
 
-/* Read and clear the plan's sticky non-physical flag (synchronises the
- * device).  *nonphysical = 1 if any kernel since the last read met rho <= 0,
- * p <= 0 or a NaN; returns GPWENO_ERR_CUDA if an earlier launch failed. */
+/* Read and clear the plan's sticky flag word (synchronises the device).
+ * Bit 0 (*nonphysical & 1) is set if any kernel since the last read met
+ * rho <= 0, p <= 0 or a NaN.  In the bounds-checked test build of the library
+ * (compiled with -DGPWENO_CHECKED) bits 1-11 record a shared-memory or global
+ * access outside its array, by access site, which that build skipped instead
+ * of making; the default build never sets them.  Returns GPWENO_ERR_CUDA if an
+ * earlier launch failed. */
 gpweno_status gpweno_flags(gpweno_plan plan, int *nonphysical);
 
 /* Batched 2D stepping (same per-face scheme as gpweno_rk3_step): one
