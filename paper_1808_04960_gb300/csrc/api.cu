@@ -700,6 +700,16 @@ gpweno_status gpweno_batch_rk3_step(gpweno_plan b, void *const *U, void *const *
     return GPWENO_OK;
 }
 
+int gpweno_plan_schedule(gpweno_plan p, int *strip_width, int *strips, int *grid, int *ctas_per_sm)
+{
+    if (!p || p->is_batch || p->dims.ndim != 2) return GPWENO_ERR_ARG;
+    if (strip_width) *strip_width = p->sched.W;
+    if (strips) *strips = p->sched.nstrips;
+    if (grid) *grid = p->sched.grid;
+    if (ctas_per_sm) *ctas_per_sm = p->sched.ctas_per_sm;
+    return GPWENO_OK;
+}
+
 int gpweno_batch_tiles(gpweno_plan b, int *strip_width_cap, int *min_rows, int *ctas_per_slot)
 {
     if (!b || !b->is_batch) return GPWENO_ERR_ARG;

@@ -167,6 +167,38 @@ StageArgs<T> base_args(const gpweno_plan_s *p)
     return a;
 }
 
+// Rows per CTA below which FP32 R = 2 grids take the three-CTA-per-SM build of the 2D kernel.
+constexpr int kWideRows = 24;
+
+// One launch of the 2D stage kernel built for MINB resident CTAs per SM: occupancy (queried
+// once per instantiation), the one-wave schedule, the launch.
+template <typename T, int R, int NT, int VAR, int MINB>
+gpweno_status launch_stage2d(gpweno_plan p, StageArgs<T> a, const TablesFor<T, R, VAR> &tb, cudaStream_t st)
+{
+    const size_t smem = stage2d_smem_bytes<T, R, NT>();
+    auto kern = stage2d_kernel<T, R, NT, VAR, MINB>;
+    static int occ = 0;   // per instantiation: resident CTAs per SM
+    if (!occ) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "stage2d smem attribute");
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+        if (e != cudaSuccess || occ < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                                                          "stage2d occupancy");
+    }
+    Schedule s = schedule2d(a.n[0], a.n[1], NT, occ * p->num_sms);
+    s.ctas_per_sm = occ;
+    a.W = s.W;
+    a.nstrips = s.nstrips;
+    a.H = s.H;
+    a.nseg = s.nseg;
+    p->sched = s;
+    cudaError_t e = launch_pdl(kern, s.grid, NT, smem, st, a, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "stage2d kernel launch");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+    return GPWENO_OK;
+}
+
 // VAR: the scheme variant (kVarMean: non-zero-mean smoothness indicators,
 // kVarFdFlux: the FD-Flux form), a compile-time switch so that the default
 // kernels keep their register budget.
@@ -222,24 +254,31 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         }
     } else if (p->dims.ndim == 2) {
         constexpr int NT = kNTxy<T>;
-        const size_t smem = stage2d_smem_bytes<T, R, NT>();
-        auto kern = stage2d_kernel<T, R, NT, VAR>;
-        static int occ = 0;   // per instantiation: resident CTAs per SM
-        if (!occ) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return cuda_fail(e, "stage2d smem attribute");
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
-            if (e != cudaSuccess || occ < 1) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
-                                                              "stage2d occupancy");
+        // FP32, default scheme, R <= 2: the build for three CTAs per SM (more registers per
+        // thread: R = 2 151 instead of 128, R = 1 132 instead of 121) is faster where the
+        // four-CTA schedule cannot fill four CTAs per SM (the grid is row-limited), and for
+        // R = 2, whose four-CTA build is register-capped, where it leaves a CTA fewer than
+        // kWideRows rows (three CTAs per SM: fewer, taller segments, fewer warm-up rows).
+        // Measured on GB300 (same-box A/B, bitwise-identical results): R = 2 x1.10 at 512^2,
+        // x1.05 at 768^2, x1.017 at 1024^2; R = 1 x1.14 at 512^2.  Not taken where it lost:
+        // R = 2 at 1536^2 (x0.995) and 4096^2 (x0.98), R = 1 at 1024^2 (x0.98), R = 3 at 1024^2
+        // (x0.986).
+        constexpr bool kHasWide = std::is_same<T, float>::value && VAR == 0 && R <= 2;
+        if constexpr (kHasWide) {
+            const int slots4 = 512 / NT * p->num_sms;
+            const Schedule s4 = schedule2d(a.n[0], a.n[1], NT, slots4);
+            const long long rows = (long long)s4.nstrips * a.n[1];
+            const bool row_limited = s4.grid < slots4;
+            const bool short_segments = R == 2 && rows < (long long)kWideRows * s4.grid;
+            if (row_limited || short_segments) {
+                gpweno_status r = launch_stage2d<T, R, NT, VAR, 3>(p, a, tb, st);
+                if (r != GPWENO_OK) return r;
+                count_launch(1);
+                return GPWENO_OK;
+            }
         }
-        Schedule s = schedule2d(a.n[0], a.n[1], NT, occ * p->num_sms);
-        a.W = s.W;
-        a.nstrips = s.nstrips;
-        a.H = s.H;
-        a.nseg = s.nseg;
-        p->sched = s;
-        cudaError_t e = launch_pdl(kern, s.grid, NT, smem, st, a, tb);
-        if (e != cudaSuccess) return cuda_fail(e, "stage2d kernel launch");
+        gpweno_status r = launch_stage2d<T, R, NT, VAR, (sizeof(T) == 4 ? 512 : 256) / NT>(p, a, tb, st);
+        if (r != GPWENO_OK) return r;
     } else {
         constexpr int NT = kNT1D;
         const size_t smem = stage1d_smem_bytes<T, R, NT>();

@@ -12,6 +12,7 @@ namespace gpweno {
 
 struct Schedule {
     int W = 0, nstrips = 0, H = 0, nseg = 0, grid = 0;
+    int ctas_per_sm = 0;   // resident CTAs per SM of the kernel build the launch used
 };
 
 }  // namespace gpweno

@@ -559,8 +559,11 @@ __device__ __forceinline__ long long balanced_start(int b, int grid, long long t
     return total;
 }
 
-template <typename T, int R, int NT, int VAR = 0>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 512 : 256) / NT) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
+// MINB: resident CTAs per SM the register budget is cut for (the default four 128-thread CTAs
+// in FP32 at 128 registers; three give the compiler ~150 registers, which pays on small grids,
+// see the host's choice in launch_stage_R).
+template <typename T, int R, int NT, int VAR = 0, int MINB = (sizeof(T) == 4 ? 512 : 256) / NT>
+__global__ void __launch_bounds__(NT, MINB) stage2d_kernel(StageArgs<T> a, TablesFor<T, R, VAR> tb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);

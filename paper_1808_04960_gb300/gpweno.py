@@ -80,6 +80,8 @@ def load(path: str | None = None):
             "gpweno_batch_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i), ctypes.POINTER(ctypes.c_ulonglong)]),
             "gpweno_batch_tiles": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "gpweno_plan_schedule": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                         ctypes.POINTER(i)]),
             "gpweno_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sigs.items():
@@ -377,6 +379,13 @@ class Plan:
         _check(self.lib.gpweno_cfl_dt(self.handle, ctypes.c_void_p(U.data_ptr()), float(cfl),
                                       ctypes.c_void_p(dt_dev.data_ptr()), _stream_handle(stream)), "gpweno_cfl_dt")
         return dt_dev
+
+    def schedule(self) -> dict:
+        """Schedule of the last 2D stage launch: strip width, strips, CTAs launched, resident CTAs
+        per SM of the kernel build used (zeros before the first launch)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self.lib.gpweno_plan_schedule(self.handle, *[ctypes.byref(x) for x in v]), "gpweno_plan_schedule")
+        return dict(strip_width=v[0].value, strips=v[1].value, grid=v[2].value, ctas_per_sm=v[3].value)
 
     def flags(self) -> int:
         v = ctypes.c_int(0)
