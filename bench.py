@@ -238,7 +238,7 @@ def run_gpu(args):
         total_ms = max_over_ranks(sum(t_list), ws)
         results[dtype] = dict(ms_per_step=total_ms / steps, steps=steps, launches_per_step=launches,
                               value=ws * cells * 3 * steps / (total_ms * 1e-3), clocks=clk.summary(),
-                              kernel_ms=statistics.mean(t_list) / 3.0)
+                              kernel_ms=statistics.mean(t_list) / 3.0, schedule=plan.schedule())
         states[dtype] = (plan, U, scratch)
         assert plan.flags() == 0, "non-physical state in benchmark run"
 
@@ -330,7 +330,9 @@ def run_gpu(args):
                      "frac": achieved / alu_peak,
                      "traffic": (kernel_traffic(f"stage2d_kernel<float,{R},128> vortex{n}")
                                  if args.graph and n == 1024 and R == 2 else None),
-                     "kernel": f"stage2d_kernel<float,{R},128>",
+                     "kernel": f"stage2d_kernel<float,{R},128> ({r32['schedule']['ctas_per_sm']}-CTA/SM build, "
+                               f"{r32['schedule']['grid']} CTAs, {r32['schedule']['strips']} strips of "
+                               f"{r32['schedule']['strip_width']} columns)",
                      "peak_kind": alu_peak_kind,
                      "flops_per_cell_stage": flops_per_cell_stage(R)},
         "roofline_hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
