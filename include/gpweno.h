@@ -332,8 +332,8 @@ int gpweno_batch_info(gpweno_plan batch, int *block, int *ctas_per_sm, int *grid
 
 /* Schedule of the last 2D stage launch of a (non-batch, 2D) plan: strip width
  * (columns), number of strips, CTAs launched, and the resident CTAs per SM of
- * the kernel build used (FP32 R <= 2 takes a three-CTA build on small grids,
- * four CTAs otherwise; FP64 one).  All zero before the first launch.  Returns
+ * the kernel build used (FP32 takes a three-CTA build on small grids, four
+ * CTAs otherwise; FP64 one).  All zero before the first launch.  Returns
  * GPWENO_ERR_ARG for batch plans and 1D or 3D plans. */
 int gpweno_plan_schedule(gpweno_plan plan, int *strip_width, int *strips, int *grid, int *ctas_per_sm);
 

@@ -254,16 +254,16 @@ gpweno_status launch_stage_R(gpweno_plan p, const StageArgs<T> &a0, cudaStream_t
         }
     } else if (p->dims.ndim == 2) {
         constexpr int NT = kNTxy<T>;
-        // FP32, default scheme (also with slab halos), R <= 2: the build for three CTAs per SM (more registers per
-        // thread: R = 2 151 instead of 128, R = 1 132 instead of 121) is faster where the
+        // FP32, default scheme (also with slab halos): the build for three CTAs per SM (more
+        // registers per thread: R = 1/2/3 132/151/163 instead of 121/128/128) is faster where the
         // four-CTA schedule cannot fill four CTAs per SM (the grid is row-limited), and for
         // R = 2, whose four-CTA build is register-capped, where it leaves a CTA fewer than
         // kWideRows rows (three CTAs per SM: fewer, taller segments, fewer warm-up rows).
         // Measured on GB300 (same-box A/B, bitwise-identical results): R = 2 x1.10 at 512^2,
-        // x1.05 at 768^2, x1.017 at 1024^2; R = 1 x1.14 at 512^2.  Not taken where it lost:
-        // R = 2 at 1536^2 (x0.995) and 4096^2 (x0.98), R = 1 at 1024^2 (x0.98), R = 3 at 1024^2
-        // (x0.986).
-        constexpr bool kHasWide = std::is_same<T, float>::value && (VAR == 0 || VAR == kVarSlab) && R <= 2;
+        // x1.05 at 768^2, x1.017 at 1024^2; R = 1 x1.14 and R = 3 x1.076 at 512^2.  Not taken
+        // where it lost: R = 2 at 1536^2 (x0.995) and 4096^2 (x0.98), R = 1 at 1024^2 (x0.98),
+        // R = 3 at 1024^2 (x0.986).
+        constexpr bool kHasWide = std::is_same<T, float>::value && (VAR == 0 || VAR == kVarSlab);
         if constexpr (kHasWide) {
             const int slots4 = 512 / NT * p->num_sms;
             const Schedule s4 = schedule2d(a.n[0], a.n[1], NT, slots4);

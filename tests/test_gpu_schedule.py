@@ -1,6 +1,6 @@
-"""The 2D launch's kernel-build choice (gpweno_plan_schedule): FP32 R <= 2 takes the build for
-three CTAs per SM where the four-CTA schedule is row-limited, and for R = 2 also where it leaves
-a CTA fewer than 24 rows; everything else takes four CTAs per SM (FP64: one 256-thread CTA)."""
+"""The 2D launch's kernel-build choice (gpweno_plan_schedule): FP32 takes the build for three
+CTAs per SM where the four-CTA schedule is row-limited, and for R = 2 also where it leaves a CTA
+fewer than 24 rows; everything else takes four CTAs per SM (FP64: one 256-thread CTA)."""
 import pytest
 
 from paper_1808_04960_gb300 import gpweno
@@ -32,7 +32,8 @@ def _sms():
                                       (512, 1, 3),
                                       (1536, 2, 4),     # ~33 rows per CTA
                                       (1024, 1, 4),     # R = 1's four-CTA build is not register-capped
-                                      (1024, 3, 4)])
+                                      (1024, 3, 4),
+                                      (512, 3, 3)])     # row-limited: every radius
 def test_build_choice(n, R, ctas):
     s = _schedule(n, R)
     assert s["ctas_per_sm"] == ctas
